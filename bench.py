@@ -1,0 +1,293 @@
+"""Benchmark: scaled-stencil apply GDoF/s and %HBM peak, plus GMG-CG time to
+relative residual 1e-8, on the unit cube split into 6 macro tetrahedra at
+level 8 (255^3 = 16.6M unknowns), k = exp(sin(pi x) cos(pi y) z).
+
+One timed step = one application of the full scaled operator (volume kernel
+fused with the interface/Dirichlet pass, one launch) in FP32 on inputs
+resident in HBM; L2 is flushed (512 MiB write) before every step, outside the
+per-step CUDA events.  The solve figures come from separate FP32+FP64-
+refinement and plain-FP64 GMG-CG solves of the manufactured problem.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs N independent replicas (the multi-GPU interface
+exchange is not built); `value` sums the replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LEVEL, COARSEST = 8, 2
+METRIC = "scaled-stencil apply GDoF/s & %HBM peak; GMG-CG time to rel. residual 1e-8"
+WORKLOAD = "unit cube, 6 Kuhn macro-tets, level 8 (257 nodes/edge), k=exp(sin(pi x)cos(pi y)z)"
+
+# ncu DRAM traffic (read+write bytes) per launch of the FP32 scaled apply on
+# this workload, with the sha256 of the kernel source it was measured on; the
+# figure is dropped (null) as soon as the kernel source changes.
+NCU_TRAFFIC = {"apply_sha": None, "bytes": None}
+
+
+def _kernel_sha():
+    p = os.path.join(ROOT, "paper_1709_06793_gb300", "csrc", "apply.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks / throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(repeats=3):
+    """The FP64 oracle's element-loop apply on the same cube and k at level 6
+    (1/512 of the level-8 work), single-threaded numpy."""
+    from oracle import hhg_oracle as O
+    from paper_1709_06793_gb300 import inputs as I
+    V, T = I.kuhn_cube()
+    lm = O.LevelMesh(O.MacroMesh(V, T), 6)
+    k = I.k_cube(lm.coords)
+    u = np.where(lm.dirichlet, 0.0, I.uniform_from_keys(I.node_keys(lm.node_gverts, lm.node_weights, lm.N), 0))
+    lm.apply(u, k, "scaled")
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        lm.apply(u, k, "scaled")
+    dt = (time.perf_counter() - t0) / repeats
+    dof = len(lm.unknowns)
+    return {"value": dof / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle element-loop scaled apply, same cube/k at level 6 ({dof} unknowns), "
+                      f"mean of {repeats}, numpy single thread"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    base = cpu_baseline(repeats=1)
+    times = []
+    from oracle import hhg_oracle as O
+    from paper_1709_06793_gb300 import inputs as I
+    V, T = I.kuhn_cube()
+    lm = O.LevelMesh(O.MacroMesh(V, T), 6)
+    k = I.k_cube(lm.coords)
+    u = np.where(lm.dirichlet, 0.0, np.sin(lm.coords[:, 0]))
+    for _ in range(args.warmup):
+        lm.apply(u, k, "scaled")
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        lm.apply(u, k, "scaled")
+        times.append(time.perf_counter() - t0)
+    dt = float(np.mean(times))
+    val = len(lm.unknowns) / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD.replace("level 8", "level 6 sample (oracle)"), "level": 6},
+           "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                            "sample": base["sample"]},
+           "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=LEVEL)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1709_06793_gb300 import build, inputs as I
+    build.build()
+    from paper_1709_06793_gb300 import hhg as H
+
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, args.level, COARSEST)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    N = 1 << args.level
+    unknowns = (N - 1) ** 3
+    H.hhg_set_coefficient(m.h, torch.tensor(I.k_cube(xyz), device="cuda"))
+    rng = np.random.default_rng(0)
+    u = torch.tensor(rng.uniform(-1, 1, n), device="cuda", dtype=torch.float32)
+    # zero Dirichlet entries: one apply of a zero-boundary vector gives the mask
+    y = torch.empty_like(u)
+    ones = torch.ones_like(u)
+    dg = torch.empty_like(u)
+    H.hhg_residual(m.h, 0, ones, torch.zeros_like(u), dg, H.HHG_F32)  # r = 1 at unknowns, 0 on Dirichlet
+    u *= dg
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32, stream)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            starts[s].record(stream)
+            H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32, stream)
+            ends[s].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    gdofs = unknowns / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    uh = u.cpu().pin_memory()
+    yh = torch.empty(n, dtype=torch.float32).pin_memory()
+    ud = torch.empty_like(u)
+    for _ in range(3):
+        ud.copy_(uh, non_blocking=True)
+        H.hhg_apply_scaled(m.h, 0, ud, y, H.HHG_F32, stream)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ke = max(5, args.steps // 5)
+    e0.record(stream)
+    for _ in range(ke):
+        ud.copy_(uh, non_blocking=True)
+        H.hhg_apply_scaled(m.h, 0, ud, y, H.HHG_F32, stream)
+        yh.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    e2e = {"value": unknowns / (e2e_ms * 1e-3) / 1e9 * world, "unit": "GDoF/s",
+           "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
+
+    peaks, src = _peaks()
+    algo_bytes = 12 * n  # read u, k; write y (FP32), every stored node
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["apply_sha"] == _kernel_sha() else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"{src} hbm_gbs (burst)",
+            "kernel": "scaled_op_kernel<float,float,APPLY>", "algorithmic_bytes_per_launch": algo_bytes}
+
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        M = None
+        f = torch.tensor(I.f_cube_sine(xyz), device="cuda") * dg.double() * (1.0 / N) ** 3
+        for name, mode in (("mixed_fp32_fp64refine", H.HHG_SOLVE_MIXED), ("fp64", H.HHG_SOLVE_FP64),
+                           ("mixed_bf16k_fp64refine", H.HHG_SOLVE_MIXED_KBF16)):
+            ud64 = torch.zeros(n, device="cuda", dtype=torch.float64)
+            H.hhg_solve(m.h, f, ud64, tol=1e-8, mode=mode, raise_on_fail=False)  # warm (setup, graphs)
+            ud64.zero_()
+            torch.cuda.synchronize()
+            st = H.hhg_solve(m.h, f, ud64, tol=1e-8, mode=mode, raise_on_fail=False)
+            solve[name] = {"ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer"],
+                           "rel_residual": st["rel_residual"], "status": st["status"]}
+        solve["metric"] = "GMG-CG (V(2,2) Jacobi) time to rel. residual 1e-8, rhs h^3 f (lumped)"
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    out = {"metric": METRIC, "value": gdofs * world, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "level": args.level, "unknowns": unknowns, "stored_nodes": n,
+                      "macro_tets": 6, "parallelism": f"replicas{world}" if world > 1 else "single",
+                      "l2": "flushed before every step (512 MiB write, outside the step events)"},
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve}
+    if rank == 0:
+        print(json.dumps(out))
+    m.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * hhg.h -- C ABI of the GB300 (sm_103a) library for the stencil-scaled P1
+ * operator -div(k grad u) on hierarchical hybrid grids.
+ *
+ * Method: a macro mesh of tetrahedra is refined uniformly (Bey's rule, paper
+ * Sec. 2.1); inside each macro tetrahedron T the nodes form the structured
+ * index space (i,j,k), i+j+k <= N = 2^level.  The operator row of a node x is
+ * its macro primitive's constant-coefficient reference stencil with every
+ * off-diagonal entry scaled by (k(x)+k(x+w))/2 and the diagonal set by the
+ * zero row sum (paper Sec. 6.1, "Cost for stencil scaling"; the bilinear form
+ * is eq. "discrete" of Sec. 2.1).  The nodal-integration operator of eq.
+ * "standardfe" / eq. "onTheFlyStencil" (Sec. 6.2) is the cost comparison.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev are CUDA device pointers that the CALLER owns; all
+ *    other pointers are host pointers the caller owns.  The library owns only
+ *    the mesh object and the workspace it allocates (at create, at
+ *    hhg_set_coefficient, or at the first call that needs it).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls are
+ *    stream-ordered and asynchronous unless stated otherwise.
+ *  - Vectors use the STORED layout at a given depth: the macro tetrahedra
+ *    active at that depth (first those above the coarsest level at that
+ *    depth, then those at it, each group in increasing tet index), each as a
+ *    packed array of its nodes ordered by k (slowest), then j, then i
+ *    (fastest); node (i,j,k)
+ *    of a tet with N = 2^level sits at
+ *        planeoff(k) + j*(N-k+1) - j*(j-1)/2 + i,
+ *        planeoff(k) = tet(N+1) - tet(N+1-k),  tet(n) = n(n+1)(n+2)/6.
+ *    Nodes on macro faces, edges and vertices are stored once per macro
+ *    tetrahedron that contains them (paper Sec. 2.1); every copy of a node
+ *    holds the same value in every input and output.  hhg_layout gives the
+ *    tet offsets.
+ *  - Depth d means refinement level level_t - d of every tet t (0 = finest).
+ *    All tets connected through a shared vertex must have the same finest
+ *    level; independent components may differ (a batch of problems).
+ *  - Dirichlet: nodes on faces that belong to exactly one macro tetrahedron
+ *    form the domain boundary with u = 0.  Inputs must hold 0 there (outputs
+ *    of this library always do); outputs are 0 there.
+ *  - Every entry point returns an hhg_status; on error, hhg_last_error()
+ *    gives a message (per calling thread).  No C++ exception crosses the ABI.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hhg_mesh_s* hhg_mesh;
+
+/* Arithmetic of a call: vector element type and coefficient (k) type. */
+typedef enum {
+    HHG_F64 = 0,       /* double vectors, double k */
+    HHG_F32 = 1,       /* float vectors, float k (k rounded once from the double input) */
+    HHG_F32_KBF16 = 2  /* float vectors, bfloat16 k (k rounded once, RN) */
+} hhg_dtype;
+
+typedef enum {
+    HHG_OK = 0,
+    HHG_ERR_ARG = -1,           /* invalid argument (message says which) */
+    HHG_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    HHG_ERR_NOMEM = -3,         /* device or host allocation failed */
+    HHG_ERR_NOT_CONVERGED = -4, /* solver hit its iteration limit */
+    HHG_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+    HHG_ERR_STATE = -6          /* call order violated (e.g. no coefficient set) */
+} hhg_status;
+
+typedef enum {
+    HHG_SMOOTH_JACOBI = 0,     /* damped Jacobi, u += omega D^-1 (f - A u) */
+    HHG_SMOOTH_CHEBYSHEV = 1,  /* Chebyshev on D^-1 A, interval [lo, hi] * lambda_max */
+    HHG_SMOOTH_LEARNED = 2     /* learned 3x3x3 convolutional correction + Jacobi */
+} hhg_smoother;
+
+typedef enum {
+    HHG_SOLVE_FP64 = 0,        /* plain FP64 GMG-preconditioned CG */
+    HHG_SOLVE_MIXED = 1,       /* FP64 iterative refinement around FP32 GMG-CG */
+    HHG_SOLVE_MIXED_KBF16 = 2  /* as MIXED, bfloat16 k in the FP32 inner solve */
+} hhg_solve_mode;
+
+typedef struct {
+    double tol;          /* stop when ||f - A u||_2 / ||f||_2 <= tol (unique unknowns) */
+    int maxit;           /* max CG iterations (FP64 mode) or total inner iterations */
+    int mode;            /* hhg_solve_mode */
+    int smoother;        /* hhg_smoother */
+    int nu1, nu2;        /* pre/post smoothing steps of the V-cycle */
+    double omega;        /* Jacobi damping (default 2/3 if <= 0) */
+    double inner_rtol;   /* MIXED: relative residual reduction of each inner solve (default 1e-4) */
+    int max_outer;       /* MIXED: max refinement steps (default 20) */
+    int use_graph;       /* capture each CG iteration in a CUDA graph (1) or launch eagerly (0) */
+} hhg_solve_params;
+
+typedef struct {
+    int iterations;      /* CG iterations (sum over refinement steps in MIXED) */
+    int outer;           /* refinement steps (1 in FP64 mode) */
+    double rel_residual; /* final ||f - A u|| / ||f|| in FP64 */
+    double time_ms;      /* wall time of the call */
+} hhg_solve_stats;
+
+/* Create a macro mesh.  verts: nv*3 doubles; tets: nt*4 vertex ids, the order
+ * of a tet's vertices is its refinement order (Bey's rule, Sec. 2.1);
+ * levels: finest refinement level per tet (coarsest_level <= level <= 10);
+ * coarsest_level: level of the dense coarse solve (>= 1).  Builds the index
+ * spaces, the 15 reference stencils per tet and level (paper Sec. 2.2, one
+ * per primitive: 4 vertices, 6 edges, 4 faces, 1 volume), the interface maps
+ * and the volume work lists, and allocates their device copies.  Errors:
+ * HHG_ERR_ARG (bad ids, degenerate tet, level mismatch across a shared
+ * vertex), HHG_ERR_NOMEM, HHG_ERR_CUDA.  Synchronous. */
+int hhg_create_macromesh(const double* verts, int nv, const int* tets, int nt,
+                         const int* levels, int coarsest_level, hhg_mesh* out);
+
+/* As hhg_create_macromesh but builds the host-side structures only (no GPU
+ * needed): hhg_num_depths, hhg_layout, hhg_node_coords and hhg_get_stencils
+ * work on it; every operator call returns HHG_ERR_STATE.  For inspection and
+ * for tests on machines without a GPU. */
+int hhg_create_macromesh_host(const double* verts, int nv, const int* tets, int nt,
+                              const int* levels, int coarsest_level, hhg_mesh* out);
+
+/* Free the mesh and every device buffer it owns.  Synchronous; NULL is a no-op. */
+int hhg_destroy_macromesh(hhg_mesh mesh);
+
+/* Number of depths (0 .. n-1) of the multigrid hierarchy. */
+int hhg_num_depths(hhg_mesh mesh, int* n);
+
+/* Stored layout at a depth.  tet_offsets: nt+1 int64 (host), offset of tet t's
+ * array (inactive tets get an empty range); tet_levels: nt ints (host), the
+ * level of tet t at this depth or -1 if inactive (either may be NULL);
+ * n_stored: total length. */
+int hhg_layout(hhg_mesh mesh, int depth, int64_t* tet_offsets, int* tet_levels, int64_t* n_stored);
+
+/* Node coordinates (host, n_stored*3 doubles) at a depth, computed from the
+ * macro vertices in increasing vertex-id order so that all copies of a node
+ * get bitwise identical coordinates. */
+int hhg_node_coords(hhg_mesh mesh, int depth, double* xyz);
+
+/* Reference stencils of tet t at a depth (host out: 16*14 doubles): row m is
+ * the primitive whose nodes lie exactly on the tet faces of bit mask m (bit f
+ * = face opposite vertex f; m = 0 is the volume), column d the direction
+ * (index space) 0..6 = e1, e2, e3, e1-e2, e1-e3, e2-e3, e1-e2+e3 and 7..13 the
+ * negatives; the value is (1/2) int_T grad phi_x . grad phi_(x+w_d), the
+ * factor 1/2 of Sec. 6.1 folded in.  Rows of absent primitives are 0. */
+int hhg_get_stencils(hhg_mesh mesh, int tet, int depth, double* out);
+
+/* Set the coefficient: k_dev is a device array of doubles in the depth-0
+ * layout, positive and equal on all copies of a node.  The library keeps
+ * its own FP64, FP32 and BF16 copies and injects them to every depth
+ * (coarse nodal value = fine nodal value at the same point).  Must precede
+ * any operator call.  Stream-ordered; allocates on first call. */
+int hhg_set_coefficient(hhg_mesh mesh, const double* k_dev, void* stream);
+
+/* y = A_s(k) u: the scaled operator (Sec. 6.1) at `depth` on all active tets.
+ * u_dev, y_dev: device arrays of the depth's stored length, element type of
+ * `dtype`; they must not overlap. */
+int hhg_apply_scaled(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
+
+/* y = A_n(k) u: the nodal-integration operator of eq. "standardfe", computed
+ * on the fly from the precomputed micro-element stiffness matrices (Sec. 6.2,
+ * eq. "onTheFlyStencil").  Same arguments as hhg_apply_scaled. */
+int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
+
+/* r = f - A_s(k) u at `depth` (the residual of the paper's benchmark, Sec. 7.4). */
+int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev,
+                 int dtype, void* stream);
+
+/* `sweeps` smoothing steps on A_s u = f at `depth`, in place on u_dev:
+ * Jacobi u += omega D^-1 (f - A u) with D the operator diagonal
+ * (-sum of the scaled off-diagonals, computed on the fly), or Chebyshev of
+ * the mesh's degree on D^-1 A.  Uses library workspace. */
+int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega,
+               const void* f_dev, void* u_dev, int dtype, void* stream);
+
+/* rc = P^T rf (restriction, depth -> depth+1) and uf += P ec (prolongation,
+ * depth+1 -> depth), P = linear interpolation between nested P1 spaces. */
+int hhg_restrict(hhg_mesh mesh, int depth, const void* rf_dev, void* rc_dev, int dtype, void* stream);
+int hhg_prolongate_add(hhg_mesh mesh, int depth, const void* ec_dev, void* uf_dev, int dtype, void* stream);
+
+/* One symmetric V(nu1,nu2) cycle for A_s u = f at depth 0, in place on u_dev. */
+int hhg_vcycle(hhg_mesh mesh, int nu1, int nu2, int smoother, const void* f_dev, void* u_dev,
+               int dtype, void* stream);
+
+/* Largest eigenvalue estimate of D^-1 A at a depth (power iteration from
+ * cos(pi N (x+y+z)) + 1/4, `its` steps, Rayleigh quotient); host out. */
+int hhg_lambda_max(hhg_mesh mesh, int depth, int its, int dtype, double* out, void* stream);
+
+/* FP64 dot product over unique unknowns (each interface node counted once). */
+int hhg_dot(hhg_mesh mesh, int depth, const void* x_dev, const void* y_dev, int dtype,
+            double* out, void* stream);
+
+/* Solve A_s(k) u = f to ||f - A u|| / ||f|| <= p->tol with GMG-preconditioned
+ * CG (FP64) or FP64 iterative refinement around FP32 GMG-CG.  f_dev, u_dev:
+ * FP64 device arrays, depth-0 layout; u_dev is the initial guess on entry and
+ * the solution on exit.  Synchronous (reads residual norms back).  Returns
+ * HHG_ERR_NOT_CONVERGED (with stats filled) if the limits are hit. */
+int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, double* u_dev,
+              hhg_solve_stats* stats, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hhg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHG_H */

@@ -1,0 +1,320 @@
+// extern "C" entry points (include/hhg.h): argument checks, error mapping.
+#include <cstring>
+#include <string>
+
+#include "hhg_internal.h"
+
+namespace hhg {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+size_t elem_size(int dtype);
+void set_coefficient(Mesh& m, const double* k, cudaStream_t s);
+void apply_scaled(Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
+void residual(Mesh& m, int depth, int dtype, const void* f, const void* u, void* r, bool nc_only, cudaStream_t s);
+void smooth(Mesh& m, int depth, int dtype, int kind, int sweeps, double omega, const void* f, void* u, bool nc_only,
+            cudaStream_t s);
+void restrict_residual(Mesh& m, int depth, int dtype, const void* rf, void* rc, cudaStream_t s);
+void prolongate_add(Mesh& m, int depth, int dtype, const void* ec, void* uf, cudaStream_t s);
+void vcycle(Mesh& m, int dtype, int nu1, int nu2, int smoother, double omega, const void* f0, void* u0, cudaStream_t s);
+void prepare(Mesh& m, int dtype, int smoother, cudaStream_t s);
+double lambda_max(Mesh& m, int depth, int its, cudaStream_t s);
+void dot(Mesh& m, int depth, int dtype, const void* x, const void* y, int slot, int post, bool nc_only, cudaStream_t s);
+int solve(Mesh& m, const hhg_solve_params& p, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s);
+void init_launch_configs(int dtype);
+}  // namespace hhg
+
+using namespace hhg;
+
+struct hhg_mesh_s {
+  Mesh* m;
+};
+
+template <class F>
+static int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return HHG_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return HHG_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return HHG_ERR_ARG;
+  } catch (...) {
+    set_error("unknown error");
+    return HHG_ERR_ARG;
+  }
+}
+
+static Mesh& need(hhg_mesh h, bool device = true) {
+  if (!h || !h->m) throw Error{HHG_ERR_ARG, "null mesh"};
+  if (device && !h->m->device) throw Error{HHG_ERR_STATE, "mesh was created host-only"};
+  return *h->m;
+}
+static void need_depth(const Mesh& m, int depth) {
+  if (depth < 0 || depth >= m.ndepth)
+    throw Error{HHG_ERR_ARG, "depth " + std::to_string(depth) + " out of range [0, " + std::to_string(m.ndepth) + ")"};
+}
+static void need_dtype(int dtype) {
+  if (dtype != HHG_F64 && dtype != HHG_F32 && dtype != HHG_F32_KBF16)
+    throw Error{HHG_ERR_ARG, "unknown dtype " + std::to_string(dtype)};
+}
+static void need_coef(const Mesh& m) {
+  if (!m.coef_set) throw Error{HHG_ERR_STATE, "hhg_set_coefficient must be called first"};
+}
+static void need_ptr(const void* p, const char* name) {
+  if (!p) throw Error{HHG_ERR_ARG, std::string(name) + " is NULL"};
+}
+
+extern "C" {
+
+int hhg_create_macromesh(const double* verts, int nv, const int* tets, int nt, const int* levels,
+                         int coarsest_level, hhg_mesh* out) {
+  return guarded([&] {
+    need_ptr(out, "out");
+    *out = nullptr;
+    Mesh* m = build_mesh(verts, nv, tets, nt, levels, coarsest_level, true);
+    *out = new hhg_mesh_s{m};
+  });
+}
+
+int hhg_create_macromesh_host(const double* verts, int nv, const int* tets, int nt, const int* levels,
+                              int coarsest_level, hhg_mesh* out) {
+  return guarded([&] {
+    need_ptr(out, "out");
+    *out = nullptr;
+    Mesh* m = build_mesh(verts, nv, tets, nt, levels, coarsest_level, false);
+    *out = new hhg_mesh_s{m};
+  });
+}
+
+int hhg_destroy_macromesh(hhg_mesh mesh) {
+  return guarded([&] {
+    if (!mesh) return;
+    if (mesh->m && mesh->m->device) cudaDeviceSynchronize();
+    free_mesh(mesh->m);
+    delete mesh;
+  });
+}
+
+int hhg_num_depths(hhg_mesh mesh, int* n) {
+  return guarded([&] {
+    need_ptr(n, "n");
+    *n = need(mesh, false).ndepth;
+  });
+}
+
+int hhg_layout(hhg_mesh mesh, int depth, int64_t* tet_offsets, int* tet_levels, int64_t* n_stored) {
+  return guarded([&] {
+    Mesh& m = need(mesh, false);
+    need_depth(m, depth);
+    const Depth& D = m.depth[depth];
+    if (tet_offsets)
+      for (int t = 0; t <= m.nt; ++t) tet_offsets[t] = D.tet_offset[t];
+    if (tet_levels)
+      for (int t = 0; t < m.nt; ++t) tet_levels[t] = D.tet_level[t];
+    if (n_stored) *n_stored = D.n_stored;
+  });
+}
+
+int hhg_node_coords(hhg_mesh mesh, int depth, double* xyz) {
+  return guarded([&] {
+    Mesh& m = need(mesh, false);
+    need_depth(m, depth);
+    need_ptr(xyz, "xyz");
+    std::vector<double> v;
+    node_coords(m, depth, v);
+    std::memcpy(xyz, v.data(), v.size() * sizeof(double));
+  });
+}
+
+int hhg_get_stencils(hhg_mesh mesh, int tet, int depth, double* out) {
+  return guarded([&] {
+    Mesh& m = need(mesh, false);
+    need_depth(m, depth);
+    need_ptr(out, "out");
+    if (tet < 0 || tet >= m.nt) throw Error{HHG_ERR_ARG, "tet out of range"};
+    const Depth& D = m.depth[depth];
+    const int s = D.tet_slot[tet];
+    if (s < 0) throw Error{HHG_ERR_ARG, "tet is not active at this depth"};
+    std::memcpy(out, &D.h_sten[(size_t)s * 16 * kNDir], 16 * kNDir * sizeof(double));
+  });
+}
+
+int hhg_set_coefficient(hhg_mesh mesh, const double* k_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_ptr(k_dev, "k_dev");
+    set_coefficient(m, k_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_apply_scaled(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_coef(m);
+    need_ptr(u_dev, "u_dev");
+    need_ptr(y_dev, "y_dev");
+    if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
+    apply_scaled(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_coef(m);
+    need_ptr(u_dev, "u_dev");
+    need_ptr(y_dev, "y_dev");
+    if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
+    launch_nodal_apply(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev, int dtype,
+                 void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_coef(m);
+    need_ptr(f_dev, "f_dev");
+    need_ptr(u_dev, "u_dev");
+    need_ptr(r_dev, "r_dev");
+    residual(m, depth, dtype, f_dev, u_dev, r_dev, false, (cudaStream_t)stream);
+  });
+}
+
+int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega, const void* f_dev, void* u_dev,
+               int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_coef(m);
+    need_ptr(f_dev, "f_dev");
+    need_ptr(u_dev, "u_dev");
+    if (sweeps < 0) throw Error{HHG_ERR_ARG, "sweeps must be >= 0"};
+    if (kind != HHG_SMOOTH_JACOBI && kind != HHG_SMOOTH_CHEBYSHEV)
+      throw Error{HHG_ERR_ARG, "hhg_smooth supports JACOBI and CHEBYSHEV"};
+    init_launch_configs(dtype);
+    smooth(m, depth, dtype, kind, sweeps, omega, f_dev, u_dev, false, (cudaStream_t)stream);
+  });
+}
+
+int hhg_restrict(hhg_mesh mesh, int depth, const void* rf_dev, void* rc_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_ptr(rf_dev, "rf_dev");
+    need_ptr(rc_dev, "rc_dev");
+    restrict_residual(m, depth, dtype, rf_dev, rc_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_prolongate_add(hhg_mesh mesh, int depth, const void* ec_dev, void* uf_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_ptr(ec_dev, "ec_dev");
+    need_ptr(uf_dev, "uf_dev");
+    prolongate_add(m, depth, dtype, ec_dev, uf_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_vcycle(hhg_mesh mesh, int nu1, int nu2, int smoother, const void* f_dev, void* u_dev, int dtype,
+               void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_dtype(dtype);
+    need_coef(m);
+    need_ptr(f_dev, "f_dev");
+    need_ptr(u_dev, "u_dev");
+    if (nu1 < 0 || nu2 < 0) throw Error{HHG_ERR_ARG, "nu1, nu2 must be >= 0"};
+    if (smoother < 0 || smoother > 2) throw Error{HHG_ERR_ARG, "unknown smoother"};
+    prepare(m, dtype, smoother, (cudaStream_t)stream);
+    vcycle(m, dtype, nu1, nu2, smoother, 2.0 / 3.0, f_dev, u_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_lambda_max(hhg_mesh mesh, int depth, int its, int dtype, double* out, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_coef(m);
+    need_ptr(out, "out");
+    (void)dtype;
+    init_launch_configs(HHG_F64);
+    m.depth[depth].lam = 0.0;
+    const int keep = m.power_its;
+    m.power_its = its;
+    *out = lambda_max(m, depth, its, (cudaStream_t)stream);
+    m.power_its = keep;
+    if (its != keep) m.depth[depth].lam = 0.0;
+  });
+}
+
+int hhg_dot(hhg_mesh mesh, int depth, const void* x_dev, const void* y_dev, int dtype, double* out, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_ptr(x_dev, "x_dev");
+    need_ptr(y_dev, "y_dev");
+    need_ptr(out, "out");
+    cudaStream_t s = (cudaStream_t)stream;
+    dot(m, depth, dtype, x_dev, y_dev, 20, 0, false, s);
+    HHG_CUDA(cudaMemcpyAsync(m.h_pinned, m.d_scalars + 20, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HHG_CUDA(cudaStreamSynchronize(s));
+    *out = m.h_pinned[0];
+  });
+}
+
+int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, double* u_dev, hhg_solve_stats* stats,
+              void* stream) {
+  int status = HHG_OK;
+  const int rc = guarded([&] {
+    Mesh& m = need(mesh);
+    need_coef(m);
+    need_ptr(p, "params");
+    need_ptr(f_dev, "f_dev");
+    need_ptr(u_dev, "u_dev");
+    if (p->smoother < 0 || p->smoother > 2) throw Error{HHG_ERR_ARG, "unknown smoother"};
+    if (p->nu1 < 0 || p->nu2 < 0) throw Error{HHG_ERR_ARG, "nu1, nu2 must be >= 0"};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t own = nullptr;
+    if (!s && p->use_graph) {  // graph capture needs a non-legacy stream
+      HHG_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+      HHG_CUDA(cudaDeviceSynchronize());
+      s = own;
+    }
+    try {
+      status = solve(m, *p, f_dev, u_dev, stats, s);
+    } catch (...) {
+      if (own) cudaStreamDestroy(own);
+      throw;
+    }
+    if (own) {
+      HHG_CUDA(cudaStreamSynchronize(own));
+      cudaStreamDestroy(own);
+    }
+  });
+  if (rc != HHG_OK) return rc;
+  if (status == HHG_ERR_NOT_CONVERGED) set_error("solver did not reach the tolerance within the iteration limits");
+  return status;
+}
+
+const char* hhg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

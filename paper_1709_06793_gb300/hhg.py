@@ -1,0 +1,249 @@
+"""Thin ctypes binding of the hhg C ABI (include/hhg.h).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors become device pointers, streams become
+cudaStream_t handles, status codes become exceptions.  All arithmetic runs in
+the CUDA library; if libhhg.so is missing the import fails loudly (there is no
+fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhhg.so")
+
+HHG_F64, HHG_F32, HHG_F32_KBF16 = 0, 1, 2
+HHG_SMOOTH_JACOBI, HHG_SMOOTH_CHEBYSHEV, HHG_SMOOTH_LEARNED = 0, 1, 2
+HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16 = 0, 1, 2
+STATUS = {0: "HHG_OK", -1: "HHG_ERR_ARG", -2: "HHG_ERR_CUDA", -3: "HHG_ERR_NOMEM",
+          -4: "HHG_ERR_NOT_CONVERGED", -5: "HHG_ERR_TIMEOUT", -6: "HHG_ERR_STATE"}
+
+
+class HHGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("mode", C.c_int), ("smoother", C.c_int),
+                ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("inner_rtol", C.c_double),
+                ("max_outer", C.c_int), ("use_graph", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("rel_residual", C.c_double),
+                ("time_ms", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1709_06793_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, L = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "hhg_create_macromesh": [P, I, P, I, P, I, C.POINTER(P)],
+        "hhg_create_macromesh_host": [P, I, P, I, P, I, C.POINTER(P)],
+        "hhg_destroy_macromesh": [P],
+        "hhg_num_depths": [P, C.POINTER(I)],
+        "hhg_layout": [P, I, P, P, C.POINTER(L)],
+        "hhg_node_coords": [P, I, P],
+        "hhg_get_stencils": [P, I, I, P],
+        "hhg_set_coefficient": [P, P, P],
+        "hhg_apply_scaled": [P, I, P, P, I, P],
+        "hhg_apply_nodal": [P, I, P, P, I, P],
+        "hhg_residual": [P, I, P, P, P, I, P],
+        "hhg_smooth": [P, I, I, I, D, P, P, I, P],
+        "hhg_restrict": [P, I, P, P, I, P],
+        "hhg_prolongate_add": [P, I, P, P, I, P],
+        "hhg_vcycle": [P, I, I, I, P, P, I, P],
+        "hhg_lambda_max": [P, I, I, I, C.POINTER(D), P],
+        "hhg_dot": [P, I, P, P, I, C.POINTER(D), P],
+        "hhg_solve": [P, C.POINTER(SolveParams), P, P, C.POINTER(SolveStats), P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.hhg_last_error.argtypes = []
+    lib.hhg_last_error.restype = C.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise HHGError(code, _lib.hhg_last_error().decode())
+    return code
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int address); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return C.c_void_p(s)
+    return C.c_void_p(s.cuda_stream)
+
+
+def _host_arrays(verts, tets, levels):
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    T = np.ascontiguousarray(tets, dtype=np.int32)
+    if np.isscalar(levels) or np.ndim(levels) == 0:
+        levels = np.full(len(T), int(levels), dtype=np.int32)
+    Lv = np.ascontiguousarray(levels, dtype=np.int32)
+    return V, T, Lv
+
+
+def hhg_create_macromesh(verts, tets, levels, coarsest_level, host_only=False):
+    V, T, Lv = _host_arrays(verts, tets, levels)
+    out = C.c_void_p()
+    f = _lib.hhg_create_macromesh_host if host_only else _lib.hhg_create_macromesh
+    _check(f(V.ctypes.data, len(V), T.ctypes.data, len(T), Lv.ctypes.data, int(coarsest_level), C.byref(out)))
+    return out
+
+
+def hhg_create_macromesh_host(verts, tets, levels, coarsest_level):
+    return hhg_create_macromesh(verts, tets, levels, coarsest_level, host_only=True)
+
+
+def hhg_destroy_macromesh(mesh):
+    _check(_lib.hhg_destroy_macromesh(mesh))
+
+
+def hhg_num_depths(mesh):
+    n = C.c_int()
+    _check(_lib.hhg_num_depths(mesh, C.byref(n)))
+    return n.value
+
+
+def hhg_layout(mesh, depth, nt):
+    off = np.zeros(nt + 1, dtype=np.int64)
+    lev = np.zeros(nt, dtype=np.int32)
+    n = C.c_int64()
+    _check(_lib.hhg_layout(mesh, depth, off.ctypes.data, lev.ctypes.data, C.byref(n)))
+    return off, lev, n.value
+
+
+def hhg_node_coords(mesh, depth, n_stored):
+    xyz = np.zeros((n_stored, 3), dtype=np.float64)
+    _check(_lib.hhg_node_coords(mesh, depth, xyz.ctypes.data))
+    return xyz
+
+
+def hhg_get_stencils(mesh, tet, depth):
+    out = np.zeros((16, 14), dtype=np.float64)
+    _check(_lib.hhg_get_stencils(mesh, tet, depth, out.ctypes.data))
+    return out
+
+
+def hhg_set_coefficient(mesh, k, stream=None):
+    _check(_lib.hhg_set_coefficient(mesh, _ptr(k), _stream(stream)))
+
+
+def hhg_apply_scaled(mesh, depth, u, y, dtype, stream=None):
+    _check(_lib.hhg_apply_scaled(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_apply_nodal(mesh, depth, u, y, dtype, stream=None):
+    _check(_lib.hhg_apply_nodal(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_residual(mesh, depth, f, u, r, dtype, stream=None):
+    _check(_lib.hhg_residual(mesh, depth, _ptr(f), _ptr(u), _ptr(r), dtype, _stream(stream)))
+
+
+def hhg_smooth(mesh, depth, kind, sweeps, omega, f, u, dtype, stream=None):
+    _check(_lib.hhg_smooth(mesh, depth, kind, sweeps, float(omega), _ptr(f), _ptr(u), dtype, _stream(stream)))
+
+
+def hhg_restrict(mesh, depth, rf, rc, dtype, stream=None):
+    _check(_lib.hhg_restrict(mesh, depth, _ptr(rf), _ptr(rc), dtype, _stream(stream)))
+
+
+def hhg_prolongate_add(mesh, depth, ec, uf, dtype, stream=None):
+    _check(_lib.hhg_prolongate_add(mesh, depth, _ptr(ec), _ptr(uf), dtype, _stream(stream)))
+
+
+def hhg_vcycle(mesh, nu1, nu2, smoother, f, u, dtype, stream=None):
+    _check(_lib.hhg_vcycle(mesh, nu1, nu2, smoother, _ptr(f), _ptr(u), dtype, _stream(stream)))
+
+
+def hhg_lambda_max(mesh, depth, its, dtype=HHG_F64, stream=None):
+    out = C.c_double()
+    _check(_lib.hhg_lambda_max(mesh, depth, its, dtype, C.byref(out), _stream(stream)))
+    return out.value
+
+
+def hhg_dot(mesh, depth, x, y, dtype, stream=None):
+    out = C.c_double()
+    _check(_lib.hhg_dot(mesh, depth, _ptr(x), _ptr(y), dtype, C.byref(out), _stream(stream)))
+    return out.value
+
+
+def hhg_solve(mesh, f, u, tol=1e-8, maxit=200, mode=HHG_SOLVE_FP64, smoother=HHG_SMOOTH_JACOBI, nu1=2, nu2=2,
+              omega=2.0 / 3.0, inner_rtol=1e-4, max_outer=20, use_graph=1, stream=None, raise_on_fail=True):
+    p = SolveParams(tol, maxit, mode, smoother, nu1, nu2, omega, inner_rtol, max_outer, use_graph)
+    st = SolveStats()
+    code = _lib.hhg_solve(mesh, C.byref(p), _ptr(f), _ptr(u), C.byref(st), _stream(stream))
+    if code != 0 and (raise_on_fail or code != -4):
+        _check(code)
+    return {"iterations": st.iterations, "outer": st.outer, "rel_residual": st.rel_residual,
+            "time_ms": st.time_ms, "status": STATUS.get(code, code)}
+
+
+class Mesh:
+    """Owning handle around hhg_create_macromesh / hhg_destroy_macromesh."""
+
+    def __init__(self, verts, tets, levels, coarsest_level, host_only=False):
+        self.verts = np.asarray(verts, dtype=np.float64)
+        self.tets = np.asarray(tets, dtype=np.int32)
+        self.nt = len(self.tets)
+        self.h = hhg_create_macromesh(verts, tets, levels, coarsest_level, host_only=host_only)
+        self.ndepth = hhg_num_depths(self.h)
+
+    def layout(self, depth=0):
+        return hhg_layout(self.h, depth, self.nt)
+
+    def n_stored(self, depth=0):
+        return self.layout(depth)[2]
+
+    def coords(self, depth=0):
+        return hhg_node_coords(self.h, depth, self.n_stored(depth))
+
+    def stencils(self, tet, depth=0):
+        return hhg_get_stencils(self.h, tet, depth)
+
+    def close(self):
+        if self.h is not None:
+            hhg_destroy_macromesh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

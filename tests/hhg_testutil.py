@@ -1,0 +1,54 @@
+"""Test helpers: enumerate the library's stored layout (documented in
+include/hhg.h) and map stored nodes to the oracle's unique nodes.  Only
+bookkeeping lives here; no operator arithmetic."""
+import numpy as np
+
+from oracle import hhg_oracle as O
+from paper_1709_06793_gb300 import inputs as I
+
+
+def stored_nodes(offsets, tet_levels):
+    """(tet, i, j, k) of every stored node at one depth, in stored order."""
+    nt = len(tet_levels)
+    order = sorted([t for t in range(nt) if tet_levels[t] >= 0], key=lambda t: offsets[t])
+    out = []
+    for t in order:
+        N = 1 << int(tet_levels[t])
+        ii, jj, kk = [], [], []
+        for k in range(N + 1):
+            for j in range(N - k + 1):
+                n = N - j - k + 1
+                ii.append(np.arange(n))
+                jj.append(np.full(n, j))
+                kk.append(np.full(n, k))
+        i = np.concatenate(ii)
+        assert offsets[t] + len(i) <= offsets[-1] or len(i) == 0
+        out.append(np.stack([np.full(len(i), t), i, np.concatenate(jj), np.concatenate(kk)], axis=1))
+    return np.concatenate(out) if out else np.zeros((0, 4), dtype=np.int64)
+
+
+def stored_keys(T, nodes, tet_levels):
+    """Key hashes (inputs.node_keys) of stored nodes."""
+    t, i, j, k = nodes.T
+    N = np.array([1 << int(tet_levels[x]) for x in t])
+    W = np.stack([N - i - j - k, i, j, k], axis=1)
+    keys = np.empty(len(t), dtype=np.uint64)
+    for n in np.unique(N):
+        sel = N == n
+        keys[sel] = I.node_keys(np.asarray(T)[t[sel]], W[sel], int(n))
+    return keys
+
+
+def oracle_map(lm, nodes):
+    """Oracle unique-node index of each stored node (single-level meshes)."""
+    t, i, j, k = nodes.T
+    out = np.empty(len(t), dtype=np.int64)
+    for tt in np.unique(t):
+        sel = t == tt
+        out[sel] = lm.local[tt][i[sel], j[sel], k[sel]]
+    assert np.all(out >= 0)
+    return out
+
+
+def oracle_keys(lm):
+    return I.node_keys(lm.node_gverts, lm.node_weights, lm.N)

@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances: FP64 rel. max-norm 1e-12 (operators; the
+smoothers and V-cycles accumulate rounding over many steps, see each test),
+FP32 rel. max-norm 1e-6 on inputs rounded to the kernel's precision."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hhg_oracle as O
+from paper_1709_06793_gb300 import inputs as I
+from tests import hhg_testutil as U
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_06793_gb300 import build
+    build.build()
+    from paper_1709_06793_gb300 import hhg
+    return hhg
+
+
+def _bf16(x):
+    """Round to bfloat16 (8 significant bits), nearest-even, directly from
+    double (as the library's conversion does); positive inputs."""
+    x = np.asarray(x, dtype=np.float64)
+    q = np.exp2(np.floor(np.log2(x)) - 7)
+    return np.round(x / q) * q
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+class Case:
+    """A mesh on the GPU plus the oracle's view of the same nodes."""
+
+    def __init__(self, H, V, T, level, coarsest, kfun, seed=0):
+        self.H = H
+        self.V, self.T, self.level = V, T, level
+        self.m = H.Mesh(V, T, level, coarsest)
+        self.off, self.lev, self.n = self.m.layout(0)
+        self.nodes = U.stored_nodes(self.off, self.lev)
+        self.lm = O.LevelMesh(O.MacroMesh(V, T), level)
+        self.idx = U.oracle_map(self.lm, self.nodes)
+        self.xyz = self.m.coords(0)
+        self.k_st = kfun(self.xyz)
+        self.k_or = kfun(self.lm.coords)
+        H.hhg_set_coefficient(self.m.h, torch.tensor(self.k_st, device="cuda"))
+        keys = U.oracle_keys(self.lm)
+        self.dir = self.lm.dirichlet
+        self.rand_or = np.where(self.dir, 0.0, I.uniform_from_keys(keys, seed))
+
+    def to_stored(self, v_or):
+        return v_or[self.idx]
+
+    def dev(self, v_or, dtype):
+        t = torch.float64 if dtype == self.H.HHG_F64 else torch.float32
+        return torch.tensor(self.to_stored(v_or), device="cuda", dtype=t)
+
+    def back(self, t):
+        """Stored GPU vector -> oracle indexing; checks all copies agree."""
+        a = t.double().cpu().numpy()
+        out = np.zeros(self.lm.n)
+        out[self.idx] = a
+        assert np.array_equal(a, out[self.idx]), "interface copies disagree"
+        return out
+
+    def kprec(self, dtype):
+        if dtype == self.H.HHG_F64:
+            return self.k_or
+        if dtype == self.H.HHG_F32:
+            return _f32(self.k_or)
+        return _bf16(self.k_or)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+MESHES = {
+    "unit_tet_l5": (I.unit_tet, 5, 3, I.k_unit_tet),
+    "kuhn_cube_l4": (I.kuhn_cube, 4, 2, I.k_cube),
+    "cube24_l3": (I.cube24, 3, 1, I.k_large),
+    "cube12_l3": (I.cube12, 3, 1, I.k_cube),
+}
+
+
+@pytest.fixture(scope="module", params=list(MESHES))
+def case(request, H):
+    mesh, level, coarsest, kf = MESHES[request.param]
+    V, T = mesh()
+    return Case(H, V, T, level, coarsest, kf)
+
+
+@pytest.mark.parametrize("kind", ["scaled", "nodal"])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_apply_parity(H, case, kind, dtype):
+    u = case.rand_or
+    tol = 1e-12 if dtype == H.HHG_F64 else 1e-6
+    uin = u if dtype == H.HHG_F64 else _f32(u)
+    ud = case.dev(uin, dtype)
+    y = torch.empty_like(ud)
+    f = H.hhg_apply_scaled if kind == "scaled" else H.hhg_apply_nodal
+    f(case.m.h, 0, ud, y, dtype)
+    torch.cuda.synchronize()
+    got = case.back(y)
+    want = case.lm.apply(uin, case.kprec(dtype), kind)
+    assert _rel(got, want) <= tol, _rel(got, want)
+    assert np.all(got[case.dir] == 0)
+
+
+def test_scaled_and_nodal_differ_for_nonaffine_k(H, case):
+    ud = case.dev(case.rand_or, H.HHG_F64)
+    ys, yn = torch.empty_like(ud), torch.empty_like(ud)
+    H.hhg_apply_scaled(case.m.h, 0, ud, ys, H.HHG_F64)
+    H.hhg_apply_nodal(case.m.h, 0, ud, yn, H.HHG_F64)
+    assert torch.max(torch.abs(ys - yn)).item() > 1e-8
+
+
+def test_residual_parity(H, case):
+    f_or = np.where(case.dir, 0.0, np.sin(7 * case.lm.coords[:, 0]) + case.lm.coords[:, 2])
+    u = case.rand_or
+    r = torch.empty(case.n, device="cuda", dtype=torch.float64)
+    H.hhg_residual(case.m.h, 0, case.dev(f_or, 0), case.dev(u, 0), r, H.HHG_F64)
+    want = np.where(case.dir, 0.0, f_or - case.lm.apply(u, case.k_or, "scaled"))
+    assert _rel(case.back(r), want) <= 1e-12
+
+
+def test_unit_tet_fifty_jacobi_sweeps(H):
+    """The small configuration: unit tetrahedron, level 5, k = 1 + 0.5 sin sin sin,
+    u ~ U[-1,1], 50 damped Jacobi sweeps (omega = 2/3), FP64, against the oracle."""
+    V, T = I.unit_tet()
+    c = Case(H, V, T, 5, 3, I.k_unit_tet)
+    A = c.lm.system(c.k_or, "scaled")
+    Dg = A.diagonal()
+    keys = U.oracle_keys(c.lm)
+    f_or = np.where(c.dir, 0.0, I.uniform_from_keys(keys, 11))
+    u = c.rand_or.copy()
+    ud = c.dev(u, 0)
+    H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_JACOBI, 50, 2.0 / 3.0, c.dev(f_or, 0), ud, H.HHG_F64)
+    uu = u[c.lm.unknowns]
+    fu = f_or[c.lm.unknowns]
+    for _ in range(50):
+        uu = uu + (2.0 / 3.0) * (fu - A @ uu) / Dg
+    want = np.zeros(c.lm.n)
+    want[c.lm.unknowns] = uu
+    assert _rel(c.back(ud), want) <= 1e-11
+
+
+def test_fp32_jacobi_sweeps(H):
+    V, T = I.kuhn_cube()
+    c = Case(H, V, T, 4, 2, I.k_cube)
+    A = c.lm.system(_f32(c.k_or), "scaled")
+    Dg = A.diagonal()
+    f_or = np.where(c.dir, 0.0, 1.0)
+    u = _f32(c.rand_or)
+    ud = c.dev(u, 1)
+    H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_JACOBI, 5, 2.0 / 3.0, c.dev(f_or, 1), ud, H.HHG_F32)
+    uu, fu = u[c.lm.unknowns], f_or[c.lm.unknowns]
+    for _ in range(5):
+        uu = uu + (2.0 / 3.0) * (fu - A @ uu) / Dg
+    want = np.zeros(c.lm.n)
+    want[c.lm.unknowns] = uu
+    assert _rel(c.back(ud), want) <= 1e-5
+
+
+def test_batched_mixed_levels_apply(H):
+    """Independent random tetrahedra with levels 3..6 in one launch: each tet
+    agrees with its own single-tet oracle."""
+    V, T = I.random_tets(6, seed=1)
+    levels = [3, 6, 4, 5, 6, 3]
+    m = H.Mesh(V, T, levels, 2)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    kf = I.k_batched(1)
+    H.hhg_set_coefficient(m.h, torch.tensor(kf(xyz), device="cuda"))
+    nodes = U.stored_nodes(off, lev)
+    u = np.zeros(n)
+    refs = []
+    for t in range(len(T)):
+        lm = O.LevelMesh(O.MacroMesh(V[4 * t:4 * t + 4], np.array([[0, 1, 2, 3]])), levels[t])
+        sel = nodes[:, 0] == t
+        loc = lm.local[0][nodes[sel, 1], nodes[sel, 2], nodes[sel, 3]]
+        ut = np.where(lm.dirichlet, 0.0, np.cos(5 * lm.coords[:, 0]) * lm.coords[:, 1] + 0.3)
+        u[sel] = ut[loc]
+        refs.append((sel, loc, lm, ut))
+    for dtype, tol in ((0, 1e-12), (1, 1e-6)):
+        tdt = torch.float64 if dtype == 0 else torch.float32
+        ud = torch.tensor(u, device="cuda", dtype=tdt)
+        y = torch.empty_like(ud)
+        H.hhg_apply_scaled(m.h, 0, ud, y, dtype)
+        got = y.double().cpu().numpy()
+        for t, (sel, loc, lm, ut) in enumerate(refs):
+            kk = kf(lm.coords)
+            if dtype == 1:
+                want = lm.apply(_f32(ut), _f32(kk), "scaled")
+            else:
+                want = lm.apply(ut, kk, "scaled")
+            assert _rel(got[sel], want[loc]) <= tol, (t, dtype)
+    m.close()
+
+
+def test_tiny_levels(H):
+    """Levels whose tets have no volume node (N <= 2) or exactly one (N = 4)."""
+    for level in (1, 2):
+        V, T = I.cube24()
+        c = Case(H, V, T, level, 1, I.k_cube)
+        ud = c.dev(c.rand_or, 0)
+        y = torch.empty_like(ud)
+        H.hhg_apply_scaled(c.m.h, 0, ud, y, 0)
+        assert _rel(c.back(y), c.lm.apply(c.rand_or, c.k_or, "scaled")) <= 1e-12
+
+
+def test_dot_counts_each_unknown_once(H, case):
+    a, b = case.rand_or, np.cos(case.lm.coords[:, 0] * 3.0)
+    b = np.where(case.dir, 0.0, b)
+    got = H.hhg_dot(case.m.h, 0, case.dev(a, 0), case.dev(b, 0), 0)
+    assert abs(got - float(a @ b)) <= 1e-12 * max(1.0, abs(float(a @ b)))
+
+
+def _hier(V, T, level, coarsest, kf, smoother="jacobi"):
+    return O.Hierarchy(V, T, level, coarsest, k_func=kf, smoother=smoother)
+
+
+def _depth_case(H, c, depth):
+    off, lev, n = c.m.layout(depth)
+    nodes = U.stored_nodes(off, lev)
+    lm = O.LevelMesh(O.MacroMesh(c.V, c.T), c.level - depth)
+    return n, lm, U.oracle_map(lm, nodes)
+
+
+def test_restrict_and_prolongate_parity(H):
+    V, T = I.cube24()
+    c = Case(H, V, T, 3, 1, I.k_large)
+    nc, lmc, idxc = _depth_case(H, c, 1)
+    P = O.prolongation(lmc, c.lm)
+    rf = c.rand_or
+    rc = torch.zeros(nc, device="cuda", dtype=torch.float64)
+    H.hhg_restrict(c.m.h, 0, c.dev(rf, 0), rc, 0)
+    want = np.where(lmc.dirichlet, 0.0, P.T @ rf)
+    got = np.zeros(lmc.n)
+    got[idxc] = rc.cpu().numpy()
+    assert _rel(got, want) <= 1e-13
+    ec = np.where(lmc.dirichlet, 0.0, np.sin(3 * lmc.coords[:, 1]))
+    uf = c.dev(c.rand_or, 0)
+    H.hhg_prolongate_add(c.m.h, 0, torch.tensor(ec[idxc], device="cuda"), uf, 0)
+    assert _rel(c.back(uf), c.rand_or + P @ ec) <= 1e-13
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_vcycle_parity_fp64(H, smoother):
+    V, T = I.kuhn_cube()
+    c = Case(H, V, T, 4, 2, I.k_cube)
+    Hh = _hier(V, T, 4, 2, I.k_cube, smoother)
+    f = np.where(c.dir, 0.0, I.f_cube_sine(c.lm.coords))
+    u0 = 0.1 * c.rand_or
+    ud = c.dev(u0, 0)
+    sm = H.HHG_SMOOTH_JACOBI if smoother == "jacobi" else H.HHG_SMOOTH_CHEBYSHEV
+    H.hhg_vcycle(c.m.h, 2, 2, sm, c.dev(f, 0), ud, 0)
+    un = Hh.vcycle(4, f[c.lm.unknowns], u0[c.lm.unknowns])
+    want = np.zeros(c.lm.n)
+    want[c.lm.unknowns] = un
+    assert _rel(c.back(ud), want) <= 1e-10
+
+
+def test_lambda_max_parity(H):
+    V, T = I.kuhn_cube()
+    c = Case(H, V, T, 4, 2, I.k_cube)
+    Hh = _hier(V, T, 4, 2, I.k_cube)
+    for depth in (0, 1):
+        lam = H.hhg_lambda_max(c.m.h, depth, 15)
+        assert abs(lam - Hh.lam[4 - depth]) <= 1e-10 * Hh.lam[4 - depth]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_solve_matches_oracle_discrete_solution(H, mode):
+    V, T = I.kuhn_cube()
+    level = 5
+    c = Case(H, V, T, level, 2, I.k_cube)
+    lm = c.lm
+    M = lm.assemble_mass()
+    f_or = np.where(c.dir, 0.0, M @ I.f_cube_sine(lm.coords))
+    kk = c.k_or if mode != 2 else _bf16(c.k_or)
+    import scipy.sparse.linalg as spla
+    A = lm.system(kk, "scaled")
+    xs = np.zeros(lm.n)
+    xs[lm.unknowns] = spla.spsolve(A.tocsc(), f_or[lm.unknowns])
+    ud = torch.zeros(c.n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(c.m.h, c.dev(f_or, 0), ud, tol=1e-10, mode=mode)
+    assert st["rel_residual"] <= 1e-10
+    got = c.back(ud)
+    err = got - xs
+    e_A = math.sqrt(abs(err[lm.unknowns] @ (A @ err[lm.unknowns])))
+    x_A = math.sqrt(xs[lm.unknowns] @ (A @ xs[lm.unknowns]))
+    assert e_A / x_A <= 1e-8
+    assert _rel(got, xs) <= 1e-7
