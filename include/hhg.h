@@ -33,6 +33,8 @@
  *  - Depth d means refinement level level_t - d of every tet t (0 = finest).
  *    All tets connected through a shared vertex must have the same finest
  *    level; independent components may differ (a batch of problems).
+ *  - Device vectors must be 16-byte aligned (they are staged with bulk copies);
+ *    allocations from cudaMalloc or PyTorch are.
  *  - Dirichlet: nodes on faces that belong to exactly one macro tetrahedron
  *    form the domain boundary with u = 0.  Inputs must hold 0 there (outputs
  *    of this library always do); outputs are 0 there.
@@ -194,6 +196,21 @@ int hhg_dot(hhg_mesh mesh, int depth, const void* x_dev, const void* y_dev, int 
  * HHG_ERR_NOT_CONVERGED (with stats filled) if the limits are hit. */
 int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, double* u_dev,
               hhg_solve_stats* stats, void* stream);
+
+/* Tuning options of a mesh (not part of the method): "kseg" planes per
+ * volume work item of the k-march and "korder" (0: longest item first, 1:
+ * items ordered by plane window) -- both rebuild the work lists and
+ * synchronise the device --, "cheb_degree", "cheb_lo", "cheb_hi" (Chebyshev interval as
+ * fractions of lambda_max) and "power_its" (lambda_max estimate).  Unknown
+ * keys or out-of-range values: HHG_ERR_ARG. */
+int hhg_set_option(hhg_mesh mesh, const char* key, double value);
+int hhg_get_option(hhg_mesh mesh, const char* key, double* value);
+
+/* Device-side error check: HHG_ERR_TIMEOUT if a kernel of this mesh hit the
+ * iteration limit of one of its bounded waits since the last check (the
+ * results of that call are invalid), HHG_OK otherwise.  Synchronous; clears
+ * the flag. */
+int hhg_device_status(hhg_mesh mesh);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hhg_last_error(void);

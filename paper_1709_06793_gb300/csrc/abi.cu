@@ -1,4 +1,5 @@
 // extern "C" entry points (include/hhg.h): argument checks, error mapping.
+#include <cstdint>
 #include <cstring>
 #include <string>
 
@@ -69,6 +70,12 @@ static void need_coef(const Mesh& m) {
 }
 static void need_ptr(const void* p, const char* name) {
   if (!p) throw Error{HHG_ERR_ARG, std::string(name) + " is NULL"};
+}
+// Vectors are staged with 16-byte bulk copies: their base must be 16-byte aligned.
+static void need_vec(const void* p, const char* name) {
+  need_ptr(p, name);
+  if (reinterpret_cast<uintptr_t>(p) % 16)
+    throw Error{HHG_ERR_ARG, std::string(name) + " must be 16-byte aligned"};
 }
 
 extern "C" {
@@ -160,8 +167,8 @@ int hhg_apply_scaled(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, i
     need_depth(m, depth);
     need_dtype(dtype);
     need_coef(m);
-    need_ptr(u_dev, "u_dev");
-    need_ptr(y_dev, "y_dev");
+    need_vec(u_dev, "u_dev");
+    need_vec(y_dev, "y_dev");
     if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
     apply_scaled(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
   });
@@ -173,8 +180,8 @@ int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, in
     need_depth(m, depth);
     need_dtype(dtype);
     need_coef(m);
-    need_ptr(u_dev, "u_dev");
-    need_ptr(y_dev, "y_dev");
+    need_vec(u_dev, "u_dev");
+    need_vec(y_dev, "y_dev");
     if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
     launch_nodal_apply(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
   });
@@ -187,9 +194,9 @@ int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev,
     need_depth(m, depth);
     need_dtype(dtype);
     need_coef(m);
-    need_ptr(f_dev, "f_dev");
-    need_ptr(u_dev, "u_dev");
-    need_ptr(r_dev, "r_dev");
+    need_vec(f_dev, "f_dev");
+    need_vec(u_dev, "u_dev");
+    need_vec(r_dev, "r_dev");
     residual(m, depth, dtype, f_dev, u_dev, r_dev, false, (cudaStream_t)stream);
   });
 }
@@ -201,8 +208,8 @@ int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega, con
     need_depth(m, depth);
     need_dtype(dtype);
     need_coef(m);
-    need_ptr(f_dev, "f_dev");
-    need_ptr(u_dev, "u_dev");
+    need_vec(f_dev, "f_dev");
+    need_vec(u_dev, "u_dev");
     if (sweeps < 0) throw Error{HHG_ERR_ARG, "sweeps must be >= 0"};
     if (kind != HHG_SMOOTH_JACOBI && kind != HHG_SMOOTH_CHEBYSHEV)
       throw Error{HHG_ERR_ARG, "hhg_smooth supports JACOBI and CHEBYSHEV"};
@@ -216,8 +223,8 @@ int hhg_restrict(hhg_mesh mesh, int depth, const void* rf_dev, void* rc_dev, int
     Mesh& m = need(mesh);
     need_depth(m, depth);
     need_dtype(dtype);
-    need_ptr(rf_dev, "rf_dev");
-    need_ptr(rc_dev, "rc_dev");
+    need_vec(rf_dev, "rf_dev");
+    need_vec(rc_dev, "rc_dev");
     restrict_residual(m, depth, dtype, rf_dev, rc_dev, (cudaStream_t)stream);
   });
 }
@@ -227,8 +234,8 @@ int hhg_prolongate_add(hhg_mesh mesh, int depth, const void* ec_dev, void* uf_de
     Mesh& m = need(mesh);
     need_depth(m, depth);
     need_dtype(dtype);
-    need_ptr(ec_dev, "ec_dev");
-    need_ptr(uf_dev, "uf_dev");
+    need_vec(ec_dev, "ec_dev");
+    need_vec(uf_dev, "uf_dev");
     prolongate_add(m, depth, dtype, ec_dev, uf_dev, (cudaStream_t)stream);
   });
 }
@@ -239,8 +246,8 @@ int hhg_vcycle(hhg_mesh mesh, int nu1, int nu2, int smoother, const void* f_dev,
     Mesh& m = need(mesh);
     need_dtype(dtype);
     need_coef(m);
-    need_ptr(f_dev, "f_dev");
-    need_ptr(u_dev, "u_dev");
+    need_vec(f_dev, "f_dev");
+    need_vec(u_dev, "u_dev");
     if (nu1 < 0 || nu2 < 0) throw Error{HHG_ERR_ARG, "nu1, nu2 must be >= 0"};
     if (smoother < 0 || smoother > 2) throw Error{HHG_ERR_ARG, "unknown smoother"};
     prepare(m, dtype, smoother, (cudaStream_t)stream);
@@ -270,8 +277,8 @@ int hhg_dot(hhg_mesh mesh, int depth, const void* x_dev, const void* y_dev, int 
     Mesh& m = need(mesh);
     need_depth(m, depth);
     need_dtype(dtype);
-    need_ptr(x_dev, "x_dev");
-    need_ptr(y_dev, "y_dev");
+    need_vec(x_dev, "x_dev");
+    need_vec(y_dev, "y_dev");
     need_ptr(out, "out");
     cudaStream_t s = (cudaStream_t)stream;
     dot(m, depth, dtype, x_dev, y_dev, 20, 0, false, s);
@@ -288,8 +295,8 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
     Mesh& m = need(mesh);
     need_coef(m);
     need_ptr(p, "params");
-    need_ptr(f_dev, "f_dev");
-    need_ptr(u_dev, "u_dev");
+    need_vec(f_dev, "f_dev");
+    need_vec(u_dev, "u_dev");
     if (p->smoother < 0 || p->smoother > 2) throw Error{HHG_ERR_ARG, "unknown smoother"};
     if (p->nu1 < 0 || p->nu2 < 0) throw Error{HHG_ERR_ARG, "nu1, nu2 must be >= 0"};
     cudaStream_t s = (cudaStream_t)stream;
@@ -313,6 +320,66 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
   if (rc != HHG_OK) return rc;
   if (status == HHG_ERR_NOT_CONVERGED) set_error("solver did not reach the tolerance within the iteration limits");
   return status;
+}
+
+int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
+  return guarded([&] {
+    Mesh& m = need(mesh, false);
+    need_ptr(key, "key");
+    const std::string k(key);
+    if (k == "kseg") {
+      set_kseg(m, (int)value, m.korder);
+    } else if (k == "korder") {
+      set_kseg(m, m.kseg, (int)value);
+    } else if (k == "cheb_degree") {
+      if (value < 1 || value > 16) throw Error{HHG_ERR_ARG, "cheb_degree must be in [1, 16]"};
+      m.cheb_degree = (int)value;
+    } else if (k == "cheb_lo") {
+      if (!(value > 0 && value < m.cheb_hi)) throw Error{HHG_ERR_ARG, "cheb_lo must be in (0, cheb_hi)"};
+      m.cheb_lo = value;
+    } else if (k == "cheb_hi") {
+      if (!(value > m.cheb_lo)) throw Error{HHG_ERR_ARG, "cheb_hi must exceed cheb_lo"};
+      m.cheb_hi = value;
+    } else if (k == "power_its") {
+      if (value < 1 || value > 1000) throw Error{HHG_ERR_ARG, "power_its must be in [1, 1000]"};
+      m.power_its = (int)value;
+      for (Depth& D : m.depth) D.lam = 0.0;
+    } else {
+      throw Error{HHG_ERR_ARG, "unknown option '" + k + "'"};
+    }
+  });
+}
+
+int hhg_get_option(hhg_mesh mesh, const char* key, double* value) {
+  return guarded([&] {
+    Mesh& m = need(mesh, false);
+    need_ptr(key, "key");
+    need_ptr(value, "value");
+    const std::string k(key);
+    if (k == "kseg") *value = m.kseg;
+    else if (k == "korder") *value = m.korder;
+    else if (k == "cheb_degree") *value = m.cheb_degree;
+    else if (k == "cheb_lo") *value = m.cheb_lo;
+    else if (k == "cheb_hi") *value = m.cheb_hi;
+    else if (k == "power_its") *value = m.power_its;
+    else throw Error{HHG_ERR_ARG, "unknown option '" + k + "'"};
+  });
+}
+
+int hhg_device_status(hhg_mesh mesh) {
+  int code = HHG_OK;
+  const int rc = guarded([&] {
+    Mesh& m = need(mesh);
+    unsigned e = 0;
+    HHG_CUDA(cudaMemcpy(&e, m.d_error, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (e) {
+      HHG_CUDA(cudaMemset(m.d_error, 0, sizeof(unsigned)));
+      code = HHG_ERR_TIMEOUT;
+    }
+  });
+  if (rc != HHG_OK) return rc;
+  if (code != HHG_OK) set_error("a device-side bounded wait ran out (results of the affected call are invalid)");
+  return code;
 }
 
 const char* hhg_last_error(void) { return g_last_error.c_str(); }

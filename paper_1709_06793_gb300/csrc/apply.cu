@@ -18,6 +18,8 @@
 // two planes of u and k live in registers; the neighbour columns i-1, i+1 are
 // loaded directly (L1 hits: the 8 lanes of a tile read contiguous memory).
 // Tiles of one warp share i0+j0 (anti-diagonal), so all 4 march equally far.
+#include <utility>
+
 #include "hhg_internal.h"
 
 namespace hhg {
@@ -75,6 +77,7 @@ struct Plane {
   typename Pair<T>::type c0[kTJ + 2];
   typename Pair<T>::type cp[kTJ + 1];
   typename Pair<T>::type cm[kTJ + 2];
+  int off[kTJ];  // tet-local offset of (i0-1, row) for the lane's rows (stores)
 };
 
 struct OpPtrs {
@@ -104,19 +107,6 @@ __device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, co
     static_cast<T*>(p.out)[idx] = ux + dn;
   } else {  // OP_DIAG
     static_cast<T*>(p.out)[idx] = diag;
-  }
-}
-
-template <class T, class KT>
-__device__ __forceinline__ void load_plane(Plane<T>& Q, const T* __restrict__ u, const KT* __restrict__ k,
-                                           int idx0, int A, int s) {
-  using P2 = typename Pair<T>::type;
-#pragma unroll
-  for (int m = 0; m < kTJ + 2; ++m) {
-    const int row = idx0 + m * A - m * (m - 1) / 2;  // (i, j0-1+m, q)
-    if (m <= s) Q.c0[m] = P2{u[row], ldk(k, row)};
-    if (m <= kTJ && m + 1 <= s) Q.cp[m] = P2{u[row + 1], ldk(k, row + 1)};
-    if (m >= 1 && m - 1 <= s) Q.cm[m] = P2{u[row - 1], ldk(k, row - 1)};
   }
 }
 
@@ -164,101 +154,315 @@ __device__ __forceinline__ void step_edges(const Plane<T>& P, const Plane<T>& Q,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Volume kernel with shared-memory staging.
+//
+// A warp owns a tile of 16 columns i0..i0+15 x 8 rows j0..j0+7 of one tet and
+// marches along k; half-warp h = lane/16 owns rows j0+4h .. j0+4h+3 of column
+// i = i0 + lane%16.  The tile's footprint in plane q is rows j0-1 .. j0+8 (m =
+// 0..9) x columns i0-1 .. i0+16 of u and k: 20 contiguous row segments.
+// Each segment is copied from its 16-byte-aligned start in 16-byte chunks
+// with cp.async (all lanes copy chunks in parallel; chunks past the end of
+// the vector are zero-filled, so no read leaves the vector).  A ring of
+// kStages planes per warp keeps kStages-2 planes in flight; completion is
+// tracked by cp.async groups (no spin loop).
+// ---------------------------------------------------------------------------
+#ifndef HHG_STAGES
+#define HHG_STAGES 4
+#endif
+constexpr int kStages = HHG_STAGES;  // staged planes per warp (kStages-2 in flight)
+constexpr int kTileI = kWarpTileI;  // columns per warp tile
+constexpr int kTileJ = kWarpTileJ;  // rows per warp tile (32/kTileI row groups x kTJ)
+constexpr int kRows = kTileJ + 2;
+
+template <class E>
+struct RowGeom {
+  static constexpr int V = 16 / (int)sizeof(E);                        // elements per 16-byte chunk
+  static constexpr int chunks = (kTileI + 2 + 2 * (V - 1) + V - 1) / V;  // max chunks per row
+  // row stride in elements: with two row groups, rows 4 apart land 16 banks
+  // apart for 4-byte data; with one group any 16-byte-multiple stride will do
+  static constexpr int stride =
+      kTileI == 16 ? (sizeof(E) == 4 ? 28 : (sizeof(E) == 8 ? 24 : 48)) : chunks * V + (sizeof(E) == 2 ? 8 : 4);
+  static constexpr int bytes = kRows * stride * (int)sizeof(E);
+  static_assert(chunks * V <= stride, "row buffer too small");
+};
+
+template <class T, class KT>
+struct Stage {
+  static constexpr int u_bytes = RowGeom<T>::bytes;
+  static constexpr int k_bytes = RowGeom<KT>::bytes;
+  static constexpr int bytes = u_bytes + k_bytes;
+  static constexpr int warp_bytes = kStages * bytes;
+  static constexpr int u_chunks = kRows * RowGeom<T>::chunks;
+  static constexpr int n_chunks = u_chunks + kRows * RowGeom<KT>::chunks;
+  static constexpr int rounds = (n_chunks + 31) / 32;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Row heads.  Offsets are tet-local (32-bit: a tet holds < 2^31 nodes); the
+// tet base is applied to the pointers once per item.  For plane q the head is
+// the offset of (i0-1, jr, q) and A the length of row jr (jr = j0-1 for the
+// tile, jb-1 for a half-warp); row jr+m starts m*A - m(m-1)/2 later.
+struct Head {
+  int e0;   // offset of (i0-1, jr, q) in the tet
+  int A;    // length of row jr in plane q
+  int Psz;  // nodes in plane q
+  int q;
+  __device__ __forceinline__ void next(int N, int jr) {  // plane q -> q+1
+    e0 += Psz - jr;
+    Psz -= N - q + 1;
+    A -= 1;
+    ++q;
+  }
+};
+
+// Per-lane copy assignment (fixed for the whole kernel): lane L < kRows
+// copies row m = L of u, lane kRows <= L < 2 kRows row m = L - kRows of k.
+// One code path for both arrays (element size chosen per lane).
+struct CopyLane {
+  int m;         // staged row
+  int tri;       // m(m-1)/2
+  unsigned dst;  // byte offset of the row in a stage
+  int lg;        // log2(element bytes)
+  bool act;
+};
+
+template <class T, class KT>
+__device__ __forceinline__ CopyLane copy_lane(int lane) {
+  CopyLane c;
+  c.act = lane < 2 * kRows;
+  const bool ku = lane < kRows;
+  c.m = ku ? lane : lane - kRows;
+  c.tri = c.m * (c.m - 1) / 2;
+  c.dst = ku ? (unsigned)(c.m * RowGeom<T>::stride * (int)sizeof(T))
+             : (unsigned)(Stage<T, KT>::u_bytes + c.m * RowGeom<KT>::stride * (int)sizeof(KT));
+  const int es = ku ? (int)sizeof(T) : (int)sizeof(KT);
+  c.lg = es == 8 ? 3 : (es == 4 ? 2 : 1);
+  return c;
+}
+
+template <class T, class KT>
+constexpr int max_chunks() {
+  return RowGeom<T>::chunks > RowGeom<KT>::chunks ? RowGeom<T>::chunks : RowGeom<KT>::chunks;
+}
+
+// Stage plane H.q: the copying lane fetches its row's 16-byte chunks from the
+// aligned start at or before column i0-1 through column i0+16.  base = the
+// lane's array (u or k) at the tet base, in bytes; bm = tet base mod V; lim =
+// elements of the vector from the tet base on (chunks are cut there).
+template <class T, class KT>
+__device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const CopyLane& cl, int N, int jm1,
+                                            int lim, int bm, const unsigned char* __restrict__ base) {
+  if (!cl.act || jm1 + cl.m > N - H.q) return;  // idle lane, or the row is absent from this plane
+  constexpr int CH = max_chunks<T, KT>();
+  const int e = H.e0 + cl.m * H.A - cl.tri;      // element (i0-1, j0-1+m, q)
+  const int vm = (16 >> cl.lg) - 1;              // V - 1
+  const int mis = (e + bm) & vm;
+  const int a = e - mis;                         // aligned start (element)
+  const int nch = ((mis + kTileI + 1) >> (4 - cl.lg)) + 1;  // chunks through column i0+16
+  const unsigned char* src = base + ((long long)a << cl.lg);
+  const unsigned dst = stage + cl.dst;
+  if ((a + CH * (16 >> cl.lg)) <= lim) {  // away from the end of the vector: whole chunks
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (c < nch) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c), "l"(src + 16 * c) : "memory");
+  } else {
+    const int rem = (lim - a) << cl.lg;  // bytes left in the vector
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (c < nch) {
+        int nb = rem - 16 * c;
+        nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+        cp_async16(dst + 16 * c, nb ? (const void*)(src + 16 * c) : (const void*)base, nb);
+      }
+    }
+  }
+}
+
+template <class E>
+__device__ __forceinline__ float elem_f(const E* p) {
+  if constexpr (sizeof(E) == 2)
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
+  else
+    return (float)*p;
+}
+
+// Lane's footprint (rows jb-1 .. jb+4, columns i-1, i, i+1) from a staged
+// plane.  hh = the half-warp's head (row jb-1); stage_lane_u / _k = the
+// lane's shared-memory bases (row 4h, column l).  Keeps the offsets of rows
+// jb .. jb+3 for the stores.
+template <class T, class KT>
+__device__ __forceinline__ void read_plane(Plane<T>& Q, const unsigned char* stage_lane_u,
+                                           const unsigned char* stage_lane_k, const Head& hh, int bmod_u,
+                                           int bmod_k) {
+  using P2 = typename Pair<T>::type;
+  using GU = RowGeom<T>;
+  using GK = RowGeom<KT>;
+#pragma unroll
+  for (int mm = 0; mm < kTJ + 2; ++mm) {
+    const int off = hh.e0 + mm * hh.A - mm * (mm - 1) / 2;  // (i0-1, jb-1+mm, q)
+    if (mm >= 1 && mm <= kTJ) Q.off[mm - 1] = off;
+    const int mis_u = (off + bmod_u) & (GU::V - 1);
+    const T* us = reinterpret_cast<const T*>(stage_lane_u) + mm * GU::stride + mis_u;
+    const KT* ks;
+    if constexpr (sizeof(KT) == sizeof(T) && GK::stride == GU::stride)  // same alignment: reuse mis
+      ks = reinterpret_cast<const KT*>(stage_lane_k) + mm * GK::stride + mis_u;
+    else
+      ks = reinterpret_cast<const KT*>(stage_lane_k) + mm * GK::stride + ((off + bmod_k) & (GK::V - 1));
+    T kv0, kv1, kv2;
+    if constexpr (sizeof(KT) == 2) {
+      kv0 = (T)elem_f(ks);
+      kv1 = (T)elem_f(ks + 1);
+      kv2 = (T)elem_f(ks + 2);
+    } else {
+      kv0 = (T)ks[0];
+      kv1 = (T)ks[1];
+      kv2 = (T)ks[2];
+    }
+    if (mm >= 1) Q.cm[mm] = P2{us[0], kv0};
+    Q.c0[mm] = P2{us[1], kv1};
+    if (mm <= kTJ) Q.cp[mm] = P2{us[2], kv2};
+  }
+}
+
+// One warp item: tile (i0, j0) of one tet, planes k0..k1 of its k-march.
 template <class T, class KT, int MODE>
-__device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, uint4 item, int lane, const OpPtrs& p) {
+__device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 item, int lane, const OpPtrs& p,
+                            unsigned char* ring, unsigned ring_s, const CopyLane& cl) {
   constexpr bool DIAG = (MODE == OP_JACOBI || MODE == OP_CHEB || MODE == OP_DIAG);
-  const int g = lane >> 3, l = lane & 7;
-  const unsigned tile = g == 0 ? item.x : (g == 1 ? item.y : (g == 2 ? item.z : item.w));
-  const int slot = (int)(item.x >> 20);
+  if (item.z < item.y) return;  // padding item: no planes
+  const unsigned tile = (unsigned)item.x;
+  const int slot = (int)(tile >> 20);
   const int j0 = (int)((tile >> 10) & 1023u), i0 = (int)(tile & 1023u);
+  const int k0 = item.y;
   const TetDev td = D.tets[slot];
   const int N = td.N;
+  const int qend = min(item.z + 1, N - (i0 + j0));
+  const int h = lane / kTileI, l = lane % kTileI;
   const int i = i0 + l;
-  // the warp marches until the tile with the smallest i0+j0 is done
-  int hmin = 2047;
-  hmin = min(hmin, (int)((item.x >> 10) & 1023u) + (int)(item.x & 1023u));
-  hmin = min(hmin, (int)((item.y >> 10) & 1023u) + (int)(item.y & 1023u));
-  hmin = min(hmin, (int)((item.z >> 10) & 1023u) + (int)(item.z & 1023u));
-  hmin = min(hmin, (int)((item.w >> 10) & 1023u) + (int)(item.w & 1023u));
-  const int qend = N - hmin;
+  const int jb = j0 + kTJ * h;  // first row of this row group
   T c[7];
 #pragma unroll
   for (int d = 0; d < 7; ++d) c[d] = sten[slot * 16 * kNDir + d];  // volume row (mask 0)
   const T* u = static_cast<const T*>(p.u) + td.base;
   const KT* k = static_cast<const KT*>(p.k) + td.base;
+  const int bmod_u = (int)(td.base & (RowGeom<T>::V - 1));
+  const int bmod_k = (int)(td.base & (RowGeom<KT>::V - 1));
+  const long long lim64 = D.n_stored - td.base;
+  const int lim = lim64 > 0x7fffffffLL ? 0x7fffffff : (int)lim64;
   OpPtrs q = p;
   q.out = static_cast<T*>(p.out) + td.base;
-  if (MODE != OP_APPLY) q.f = static_cast<const T*>(p.f) + td.base;
+  if (MODE != OP_APPLY && MODE != OP_DIAG) q.f = static_cast<const T*>(p.f) + td.base;
   if (MODE == OP_CHEB) {
     q.d_in = static_cast<const T*>(p.d_in) + td.base;
     q.d_out = static_cast<T*>(p.d_out) + td.base;
   }
-  // plane 0
-  int Psz = (N + 1) * (N + 2) / 2;                          // nodes in plane q
-  int A = N - j0 + 2;                                        // length of row j0-1 in plane q
-  int idx0 = (j0 - 1) * (N + 1) - (j0 - 1) * (j0 - 2) / 2 + i;  // (i, j0-1, q)
-  int s = N - i - j0 + 1;                                    // valid iff c + m <= s
-  Plane<T> PA, PB;
-#pragma unroll
-  for (int m = 0; m < kTJ + 2; ++m) {
-    PA.c0[m] = PB.c0[m] = {0, 0};
-    PA.cm[m] = PB.cm[m] = {0, 0};
+  // copy head (tile rows from j0-1) and read head (this half's rows from jb-1) at plane k0-1
+  Head ch, rh;
+  {
+    const int qq = k0 - 1;
+    const int M = N - qq;
+    ch.q = rh.q = qq;
+    ch.Psz = rh.Psz = (M + 1) * (M + 2) / 2;
+    const int pl = (int)(tetnum(N + 1) - tetnum(N + 1 - qq));
+    ch.A = M - j0 + 2;
+    ch.e0 = pl + (j0 - 1) * (M + 1) - (j0 - 1) * (j0 - 2) / 2 + (i0 - 1);
+    rh.A = M - jb + 2;
+    rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1);
   }
-#pragma unroll
-  for (int m = 0; m < kTJ + 1; ++m) PA.cp[m] = PB.cp[m] = {0, 0};
-  load_plane<T, KT>(PA, u, k, idx0, A, s);
-  Acc<T, DIAG> yA[kTJ], yB[kTJ];
-  int prev_idx0 = idx0, prev_A = A;
-  auto advance = [&](int qn) {  // move the plane state from qn-1 to qn
-    prev_idx0 = idx0;
-    prev_A = A;
-    idx0 += Psz - (j0 - 1);
-    Psz -= N - qn + 2;
-    A -= 1;
-    s -= 1;
+  constexpr int SB = Stage<T, KT>::bytes;
+  // this lane's copy source (u or k at the tet base) and base alignment
+  const bool lane_copies_u = lane < kRows;
+  const unsigned char* cbase = lane_copies_u ? reinterpret_cast<const unsigned char*>(u)
+                                             : reinterpret_cast<const unsigned char*>(k);
+  const int cbm = lane_copies_u ? bmod_u : bmod_k;
+  const int lane_u = (kTJ * h * RowGeom<T>::stride + l) * (int)sizeof(T);  // row 4h, column l
+  const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
+  int st_c = 0, st_r = 0;  // stage of the next plane to copy / to read
+  auto issue_next = [&]() {  // stage plane ch.q if the march needs it; one group per plane
+    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, cbm, cbase);
+    cp_async_commit();
+    ch.next(N, j0 - 1);
+    st_c = st_c + 1 == kStages ? 0 : st_c + 1;
   };
+  auto read_next = [&](Plane<T>& P) {
+    const unsigned char* sb = ring + st_r * SB;
+    read_plane<T, KT>(P, sb + lane_u, sb + lane_k, rh, bmod_u, bmod_k);
+    rh.next(N, jb - 1);
+    st_r = st_r + 1 == kStages ? 0 : st_r + 1;
+  };
+#pragma unroll
+  for (int t = 0; t < kStages - 1; ++t) issue_next();  // planes k0-1 .. k0+kStages-3
+  cp_async_wait<kStages - 2>();
+  __syncwarp();
+  Plane<T> X, Y;
+  read_next(X);  // plane k0-1
+  Acc<T, DIAG> yX[kTJ], yY[kTJ];
   auto store = [&](const Plane<T>& P, Acc<T, DIAG>(&y)[kTJ], int pl) {
-    if (pl < 1) return;
+    const int lim_r = N - 1 - i - jb - pl;  // row r holds a volume node iff r <= lim_r
 #pragma unroll
-    for (int r = 0; r < kTJ; ++r) {
-      if (i + j0 + r + pl <= N - 1) {
-        const int m = r + 1;
-        const long long idx = prev_idx0 + m * prev_A - m * (m - 1) / 2;
-        finish_node<T, MODE>(y[r].y, y[r].d, P.c0[m].x, idx, q);
-      }
-    }
+    for (int r = 0; r < kTJ; ++r)
+      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r] + l + 1, q);
   };
-  for (int qq = 1; qq <= qend; qq += 2) {
-    advance(qq);
-    load_plane<T, KT>(PB, u, k, idx0, A, s);
-    step_edges<T, DIAG>(PA, PB, c, yA, yB);
-    store(PA, yA, qq - 1);
+  auto step = [&](Plane<T>& P, Plane<T>& Q, Acc<T, DIAG>(&yP)[kTJ], Acc<T, DIAG>(&yQ)[kTJ], int qq) {
+    __syncwarp();                  // every lane has read plane qq-2 before its stage is refilled
+    issue_next();                  // plane qq + kStages - 2
+    cp_async_wait<kStages - 2>();  // this lane's copies of plane qq have landed
+    __syncwarp();                  // ... and every other lane's
+    read_next(Q);                  // plane qq
+    step_edges<T, DIAG>(P, Q, c, yP, yQ);
+    if (qq - 1 >= k0) store(P, yP, qq - 1);
+  };
+  for (int qq = k0; qq <= qend; qq += 2) {
+    step(X, Y, yX, yY, qq);
     if (qq + 1 > qend) break;
-    advance(qq + 1);
-    load_plane<T, KT>(PA, u, k, idx0, A, s);
-    step_edges<T, DIAG>(PB, PA, c, yB, yA);
-    store(PB, yB, qq);
+    step(Y, X, yY, yX, qq + 1);
   }
+  cp_async_wait<0>();
+  __syncwarp();
 }
 
-// Partial row of one stored copy (its tet's micro-elements only).
+// Partial row of one stored copy (its tet's micro-elements only).  Neighbour
+// offsets: plane starts P(k) and row starts within planes k-1, k, k+1 are
+// formed once; the 14 directions then only add constants.
 template <class T, class KT>
 __device__ __forceinline__ void scaled_partial(const DepthDev& D, const T* __restrict__ sten, const BCopy& cp,
                                                const T* __restrict__ u, const KT* __restrict__ k, T& y, T& diag) {
   const TetDev td = D.tets[cp.slot];
   const int N = td.N;
   const T* st = sten + (cp.slot * 16 + cp.mask) * kNDir;
-  const T ux = u[cp.idx];
-  const T kx = ldk(k, cp.idx);
+  const T* ut = u + td.base;
+  const KT* kt = k + td.base;
+  const int ci = cp.i, cj = cp.j, ck = cp.k;
+  // plane start of plane kk and start of row jj in it
+  auto pstart = [&](int kk) { return (int)(tetnum(N + 1) - tetnum(N + 1 - kk)); };
+  auto rstart = [&](int pk, int kk, int jj) { return pk + jj * (N - kk + 1) - jj * (jj - 1) / 2; };
+  const int p0 = pstart(ck);
+  const int pm = ck > 0 ? pstart(ck - 1) : 0;
+  const int pp = ck < N ? pstart(ck + 1) : 0;
+  const int x = rstart(p0, ck, cj) + ci;
+  const T ux = ut[x];
+  const T kx = (T)ldk(kt, x);
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) {
     int di, dj, dk;
     dir_of(d, di, dj, dk);
-    const int a = cp.i + di, b = cp.j + dj, cc = cp.k + dk;
+    const int a = ci + di, b = cj + dj, cc = ck + dk;
     if (a < 0 || b < 0 || cc < 0 || a + b + cc > N) continue;
-    const long long idx = td.base + node_offset(N, a, b, cc);
-    const T sv = st[d] * (kx + (T)ldk(k, idx));
-    y = fma(sv, u[idx] - ux, y);
+    const int ps = dk == 0 ? p0 : (dk < 0 ? pm : pp);
+    const int idx = rstart(ps, cc, b) + a;
+    const T sv = st[d] * (kx + (T)ldk(kt, idx));
+    y = fma(sv, ut[idx] - ux, y);
     diag -= sv;
   }
 }
@@ -304,33 +508,57 @@ __device__ void boundary_node(const DepthDev& D, const T* __restrict__ sten, int
 }
 
 // Persistent kernel: warps take volume items (longest first), then chunks of
-// 32 interface nodes.
+// 32 interface nodes.  Dynamic shared memory: one staging ring per warp.
 template <class T, class KT, int MODE>
-__global__ void __launch_bounds__(128) scaled_op_kernel(DepthDev D, OpPtrs p, int n_items, int n_bnodes) {
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) scaled_op_kernel(DepthDev D, OpPtrs p, int n_items, int n_bnodes,
+                                                            unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  (void)err;
   const T* sten = nullptr;
   if constexpr (sizeof(T) == 8)
     sten = reinterpret_cast<const T*>(D.sten64);
   else
     sten = reinterpret_cast<const T*>(D.sten32);
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned char* ring = smem_raw + wib * Stage<T, KT>::warp_bytes;
+  const unsigned ring_s = smem_addr(ring);
+  const CopyLane cl = copy_lane<T, KT>(lane);
+  // Work in quads of 4 positions (one per warp of a block): volume quads
+  // (4 consecutive items: the work list groups j-stacked tiles in fours) and
+  // interface quads (4 chunks of 32 nodes) spread evenly among them.
   const int nchunks = (n_bnodes + 31) / 32;
-  for (int it = warp; it < n_items + nchunks; it += nwarps) {
-    if (it < n_items) {
-      volume_item<T, KT, MODE>(D, sten, D.items[it], lane, p);
-    } else {
-      const int b = (it - n_items) * 32 + lane;
+  const int vq = (n_items + 3) / 4, bq = (nchunks + 3) / 4;
+  const int totq = vq + bq;
+  const int R = bq ? max(1, totq / bq) : totq + 1;
+  for (int it = warp; it < 4 * totq; it += nwarps) {
+    const int qd = it >> 2, sub = it & 3;
+    const int before = min(bq, qd / R);  // interface quads before this one
+    if (qd % R == R - 1 && qd / R < bq) {
+      const int b = ((qd / R) * 4 + sub) * 32 + lane;
       if (b < n_bnodes) boundary_node<T, KT, MODE>(D, sten, b, p);
+    } else {
+      const int v = (qd - before) * 4 + sub;
+      if (v < n_items) volume_item<T, KT, MODE>(D, sten, D.items[v], lane, p, ring, ring_s, cl);
     }
   }
+}
+
+template <class T, class KT>
+constexpr int ring_bytes() {
+  return 4 * Stage<T, KT>::warp_bytes;  // 4 warps per block
 }
 
 template <class T, class KT, int MODE>
 static int occupancy() {
   static int occ = 0;
   if (!occ) {
-    HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scaled_op_kernel<T, KT, MODE>, 128, 0));
+    HHG_CUDA(cudaFuncSetAttribute(scaled_op_kernel<T, KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ring_bytes<T, KT>()));
+    HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scaled_op_kernel<T, KT, MODE>, 128,
+                                                           ring_bytes<T, KT>()));
     if (occ < 1) occ = 1;
   }
   return occ;
@@ -366,7 +594,7 @@ static void launch_typed(const Mesh& m, int depth, const OpArgs& a, const void* 
   const int occ = occupancy<T, KT, MODE>();
   const int blocks = std::min((work + 3) / 4, m.num_sms * occ);
   OpPtrs p{a.u, kptr, a.f, a.out, a.d_in, a.d_out, a.omega, a.ca, a.cb};
-  scaled_op_kernel<T, KT, MODE><<<blocks, 128, 0, s>>>(D, p, n_items, n_b);
+  scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, n_b, m.d_error);
   HHG_CUDA(cudaGetLastError());
 }
 
@@ -522,13 +750,209 @@ __global__ void nodal_boundary_kernel(DepthDev D, const T* __restrict__ u, const
   for (int q = lo; q < hi; ++q) y[D.bcopies[q].idx] = v;
 }
 
+// Staged nodal-integration volume kernel: the same tiles, work list and
+// shared-memory staging as the scaled kernel, but three planes in registers
+// (q-2, q-1, q): the 24 micro tets around a node of plane q-1 span planes
+// q-2 .. q.  The tet's element matrices (6 Kuhn types, symmetric, 36 distinct
+// off-diagonal entries of (1/4) A_t) are held in registers; every micro tet
+// of every node is unrolled at compile time.
+constexpr NodalTable kNodalC = make_nodal_table();
+
+template <int S, int V, int W>
+struct EIdx {  // register slot of (1/4) A_sigma[v][w], v != w (symmetric pairs share a slot)
+  static constexpr int a = V < W ? V : W, b = V < W ? W : V;
+  static constexpr int pair = a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);  // (0,1)..(0,3)->0..2, (1,2)->3, (1,3)->4, (2,3)->5
+  static constexpr int value = S * 6 + pair;
+};
+
+template <int DI, int MM, class P2, class T>
+__device__ __forceinline__ P2 plane_at(const Plane<T>& P) {
+  if constexpr (DI == 0)
+    return P.c0[MM];
+  else if constexpr (DI > 0)
+    return P.cp[MM];
+  else
+    return P.cm[MM];
+}
+
+template <int DK, int DI, int MM, class T>
+__device__ __forceinline__ typename Pair<T>::type at3(const Plane<T>& A, const Plane<T>& B, const Plane<T>& C) {
+  using P2 = typename Pair<T>::type;
+  if constexpr (DK < 0)
+    return plane_at<DI, MM, P2>(A);
+  else if constexpr (DK == 0)
+    return plane_at<DI, MM, P2>(B);
+  else
+    return plane_at<DI, MM, P2>(C);
+}
+
+// contribution of micro tet E of node row R: ksum * sum_w A[v][w] (u_w - u_x)
+template <int E, int R, class T>
+__device__ __forceinline__ T nodal_term(const Plane<T>& A, const Plane<T>& B, const Plane<T>& C, const T (&el)[36],
+                                        T ux, T kx) {
+  constexpr NodalEntry en = kNodalC.e[E];
+  constexpr int v = en.v;
+  T ks = kx, inner = 0;
+#define HHG_NODAL_VERT(QQ)                                                                              \
+  if constexpr (QQ != v) {                                                                            \
+    constexpr int di = en.off[QQ][0], dj = en.off[QQ][1], dk = en.off[QQ][2];                          \
+    const auto w = at3<dk, di, R + 1 + dj, T>(A, B, C);                                                 \
+    ks += w.y;                                                                                          \
+    inner = fma(el[EIdx<en.sigma, v, QQ>::value], w.x - ux, inner);                                    \
+  }
+  HHG_NODAL_VERT(0)
+  HHG_NODAL_VERT(1)
+  HHG_NODAL_VERT(2)
+  HHG_NODAL_VERT(3)
+#undef HHG_NODAL_VERT
+  return ks * inner;
+}
+
+template <int R, class T, int... E>
+__device__ __forceinline__ T nodal_row(const Plane<T>& A, const Plane<T>& B, const Plane<T>& C, const T (&el)[36],
+                                       std::integer_sequence<int, E...>) {
+  const T ux = B.c0[R + 1].x, kx = B.c0[R + 1].y;
+  T y = 0;
+  ((y += nodal_term<E, R, T>(A, B, C, el, ux, kx)), ...);
+  return y;
+}
+
+template <class T, class KT>
+__device__ void nodal_item(const DepthDev& D, const T* __restrict__ elem, int4 item, int lane, const OpPtrs& p,
+                           unsigned char* ring, unsigned ring_s, const CopyLane& cl) {
+  if (item.z < item.y) return;  // padding item: no planes
+  const unsigned tile = (unsigned)item.x;
+  const int slot = (int)(tile >> 20);
+  const int j0 = (int)((tile >> 10) & 1023u), i0 = (int)(tile & 1023u);
+  const int k0 = item.y;
+  const TetDev td = D.tets[slot];
+  const int N = td.N;
+  const int qend = min(item.z + 1, N - (i0 + j0));
+  const int h = lane / kTileI, l = lane % kTileI;
+  const int i = i0 + l;
+  const int jb = j0 + kTJ * h;
+  T el[36];
+#pragma unroll
+  for (int s6 = 0; s6 < 6; ++s6) {
+    const T* E = elem + slot * 96 + s6 * 16;
+    el[s6 * 6 + 0] = E[1];
+    el[s6 * 6 + 1] = E[2];
+    el[s6 * 6 + 2] = E[3];
+    el[s6 * 6 + 3] = E[6];
+    el[s6 * 6 + 4] = E[7];
+    el[s6 * 6 + 5] = E[11];
+  }
+  const T* u = static_cast<const T*>(p.u) + td.base;
+  const KT* k = static_cast<const KT*>(p.k) + td.base;
+  T* out = static_cast<T*>(p.out) + td.base;
+  const int bmod_u = (int)(td.base & (RowGeom<T>::V - 1));
+  const int bmod_k = (int)(td.base & (RowGeom<KT>::V - 1));
+  const long long lim64 = D.n_stored - td.base;
+  const int lim = lim64 > 0x7fffffffLL ? 0x7fffffff : (int)lim64;
+  Head ch, rh;
+  {
+    const int qq = k0 - 1;
+    const int M = N - qq;
+    ch.q = rh.q = qq;
+    ch.Psz = rh.Psz = (M + 1) * (M + 2) / 2;
+    const int pl = (int)(tetnum(N + 1) - tetnum(N + 1 - qq));
+    ch.A = M - j0 + 2;
+    ch.e0 = pl + (j0 - 1) * (M + 1) - (j0 - 1) * (j0 - 2) / 2 + (i0 - 1);
+    rh.A = M - jb + 2;
+    rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1);
+  }
+  constexpr int SB = Stage<T, KT>::bytes;
+  const bool lane_copies_u = lane < kRows;
+  const unsigned char* cbase = lane_copies_u ? reinterpret_cast<const unsigned char*>(u)
+                                             : reinterpret_cast<const unsigned char*>(k);
+  const int cbm = lane_copies_u ? bmod_u : bmod_k;
+  const int lane_u = (kTJ * h * RowGeom<T>::stride + l) * (int)sizeof(T);
+  const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
+  int st_c = 0, st_r = 0;
+  auto issue_next = [&]() {
+    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, cbm, cbase);
+    cp_async_commit();
+    ch.next(N, j0 - 1);
+    st_c = st_c + 1 == kStages ? 0 : st_c + 1;
+  };
+  auto read_next = [&](Plane<T>& P) {
+    const unsigned char* sb = ring + st_r * SB;
+    read_plane<T, KT>(P, sb + lane_u, sb + lane_k, rh, bmod_u, bmod_k);
+    rh.next(N, jb - 1);
+    st_r = st_r + 1 == kStages ? 0 : st_r + 1;
+  };
+#pragma unroll
+  for (int t = 0; t < kStages - 1; ++t) issue_next();
+  Plane<T> X, Y, Z;
+  cp_async_wait<kStages - 2>();
+  __syncwarp();
+  read_next(X);  // plane k0-1
+  __syncwarp();
+  issue_next();
+  cp_async_wait<kStages - 2>();
+  __syncwarp();
+  read_next(Y);  // plane k0
+  auto step = [&](const Plane<T>& A, const Plane<T>& B, Plane<T>& C, int qq) {
+    __syncwarp();
+    issue_next();
+    cp_async_wait<kStages - 2>();
+    __syncwarp();
+    read_next(C);  // plane qq
+    const int pl = qq - 1;
+    const int lim_r = N - 1 - i - jb - pl;
+    constexpr auto seq = std::make_integer_sequence<int, 24>{};
+    const T y0 = nodal_row<0>(A, B, C, el, seq);
+    const T y1 = nodal_row<1>(A, B, C, el, seq);
+    const T y2 = nodal_row<2>(A, B, C, el, seq);
+    const T y3 = nodal_row<3>(A, B, C, el, seq);
+    if (0 <= lim_r) out[B.off[0] + l + 1] = y0;
+    if (1 <= lim_r) out[B.off[1] + l + 1] = y1;
+    if (2 <= lim_r) out[B.off[2] + l + 1] = y2;
+    if (3 <= lim_r) out[B.off[3] + l + 1] = y3;
+  };
+  for (int qq = k0 + 1; qq <= qend; qq += 3) {
+    step(X, Y, Z, qq);
+    if (qq + 1 > qend) break;
+    step(Y, Z, X, qq + 1);
+    if (qq + 2 > qend) break;
+    step(Z, X, Y, qq + 2);
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+template <class T, class KT>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 3) nodal_staged_kernel(DepthDev D, OpPtrs p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const T* elem;
+  if constexpr (sizeof(T) == 8)
+    elem = reinterpret_cast<const T*>(D.elem64);
+  else
+    elem = reinterpret_cast<const T*>(D.elem32);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned char* ring = smem_raw + wib * Stage<T, KT>::warp_bytes;
+  const unsigned ring_s = smem_addr(ring);
+  const CopyLane cl = copy_lane<T, KT>(lane);
+  for (int it = warp; it < D.n_items; it += nwarps) nodal_item<T, KT>(D, elem, D.items[it], lane, p, ring, ring_s, cl);
+}
+
 template <class T, class KT>
 static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk, void* y, cudaStream_t s) {
   const DepthDev& D = m.depth[depth].dev;
-  if (D.n_rows > 0) {
-    const int blocks = std::min((D.n_rows + 7) / 8, m.num_sms * 8);
-    nodal_volume_kernel<T, KT><<<blocks, 256, 0, s>>>(D, static_cast<const T*>(u), static_cast<const KT*>(kk),
-                                                       static_cast<T*>(y));
+  if (D.n_items > 0) {
+    static int occ = 0;
+    const int smem = 4 * Stage<T, KT>::warp_bytes;
+    if (!occ) {
+      HHG_CUDA(cudaFuncSetAttribute(nodal_staged_kernel<T, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, nodal_staged_kernel<T, KT>, 128, smem));
+      if (occ < 1) occ = 1;
+    }
+    const int blocks = std::min((D.n_items + 3) / 4, m.num_sms * occ);
+    OpPtrs p{u, kk, nullptr, y, nullptr, nullptr, 0, 0, 0};
+    nodal_staged_kernel<T, KT><<<blocks, 128, smem, s>>>(D, p);
     HHG_CUDA(cudaGetLastError());
   }
   if (D.n_bnodes > 0) {

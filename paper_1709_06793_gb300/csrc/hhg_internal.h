@@ -15,7 +15,11 @@ namespace hhg {
 constexpr int kNDir = 14;     // stencil directions (without the centre)
 constexpr int kMaxLevel = 10; // N <= 1024: i, j, k fit in 11 bits
 constexpr int kTJ = 4;        // rows per thread in the volume kernels
-constexpr int kTI = 8;        // lanes per tile (consecutive i)
+#ifndef HHG_TILE_I
+#define HHG_TILE_I 16
+#endif
+constexpr int kWarpTileI = HHG_TILE_I;       // columns of a volume warp tile (16 or 32)
+constexpr int kWarpTileJ = 32 / HHG_TILE_I * kTJ;  // rows of a volume warp tile
 
 // Direction d = (di, dj, dk) in the index space of a macro tet.
 // 0..6: e1, e2, e3, e1-e2, e1-e3, e2-e3, e1-e2+e3 (the 7 edge directions of
@@ -65,7 +69,7 @@ struct DepthDev {
   const float* sten32;
   const double* elem64;  // [slot][6][16]   (1/4)*micro-element stiffness per Kuhn type
   const float* elem32;
-  const uint4* items;    // volume work: 4 tiles per warp item
+  const int4* items;     // volume work: (tile = slot<<20 | j0<<10 | i0, k0, k1, -) per warp item
   int n_items;           // items of all active tets
   int n_items_nc;        // items of tets above the coarsest level (prefix)
   const int* bstart;     // boundary unique nodes: copies bstart[b]..bstart[b+1]
@@ -96,7 +100,7 @@ struct Depth {
   std::vector<TetDev> h_tets;
   std::vector<double> h_sten;         // [slot][16][14]
   std::vector<double> h_elem;         // [slot][6][16]
-  std::vector<uint4> h_items;
+  std::vector<int4> h_items;
   int n_items = 0, n_items_nc = 0;
   std::vector<int> h_bstart;
   std::vector<BCopy> h_bcopies;
@@ -162,6 +166,7 @@ struct Mesh {
   // scratch
   double* d_red = nullptr;        // reduction partials
   unsigned* d_counter = nullptr;
+  unsigned* d_error = nullptr;    // set by a kernel whose bounded wait ran out
   double* d_scalars = nullptr;    // device scalars for CG
   double* h_pinned = nullptr;     // pinned host scalars
   double* d_geom = nullptr;       // macro vertices (double) followed by tets (int)
@@ -169,6 +174,8 @@ struct Mesh {
   int cheb_degree = 2;
   double cheb_lo = 0.3, cheb_hi = 1.1;
   int power_its = 15;
+  int kseg = 32;                  // planes per volume work item (k-march segment)
+  int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)
   void* learned = nullptr;
 };
@@ -200,6 +207,8 @@ void node_coords(const Mesh& m, int depth, std::vector<double>& xyz);
 void stencils_for(const Mesh& m, int tet, int level, double* out16x14);
 void elements_for(const Mesh& m, int tet, int level, double* out6x16);
 void* dalloc(Depth& d, size_t bytes);
+void build_items(const Mesh& m, Depth& D);
+void set_kseg(Mesh& m, int kseg, int korder);
 
 // ---- kernels (apply.cu / mg.cu) ----------------------------------------------
 enum OpMode { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_CHEB = 3, OP_DIAG = 4 };

@@ -248,6 +248,64 @@ static int find(std::vector<int>& p, int x) {
   return x;
 }
 
+// Volume work list: tiles of kTI x kTJ columns (i0, j0), 4 per warp item (one
+// tet per item, equal i0+j0 where possible), each tile's k-march cut into
+// segments of m.kseg planes; longest item first.
+void build_items(const Mesh& m, Depth& D) {
+  const int ns = (int)D.slot_tet.size();
+  const int empty_tile = 1023 << 10 | 1023;
+  std::vector<std::vector<int4>> by_class(2);
+  for (int cls = 0; cls < 2; ++cls) {
+    std::vector<std::pair<long long, int4>> its;  // (sort key, item)
+    for (int s = 0; s < ns; ++s) {
+      if ((s < D.n_slots_nc) != (cls == 0)) continue;
+      const int N = D.h_tets[s].N;
+      if (m.korder == 2) {
+        // quads: the 4 warps of a block take 4 tiles stacked in j (same i0,
+        // same plane window), so the halo rows they share are fetched once
+        const int jstack = 4 * kWarpTileJ;
+        for (int k0 = 1; k0 <= N - 3; k0 += m.kseg)
+          for (int jg = 1; jg <= N - 2; jg += jstack)
+            for (int i0 = 1; i0 + jg <= N - 2; i0 += kWarpTileI) {
+              int4 q[4];
+              int live = 0;
+              for (int w = 0; w < 4; ++w) {
+                const int j0 = jg + w * kWarpTileJ;
+                const int top = N - 1 - (i0 + j0);
+                if (j0 <= N - 2 && top >= k0) {
+                  q[w] = make_int4(s << 20 | j0 << 10 | i0, k0, std::min(top, k0 + m.kseg - 1), 0);
+                  ++live;
+                } else {
+                  q[w] = make_int4(s << 20 | empty_tile, 1, 0, 0);  // no planes
+                }
+              }
+              if (!live) continue;
+              const long long key = ((long long)k0 << 40) | ((long long)s << 28) | ((long long)i0 << 14) | jg;
+              for (int w = 0; w < 4; ++w) its.push_back({key, q[w]});
+            }
+      } else {
+        for (int j0 = 1; j0 <= N - 2; j0 += kWarpTileJ)
+          for (int i0 = 1; i0 + j0 <= N - 2; i0 += kWarpTileI) {
+            const int tile = s << 20 | j0 << 10 | i0;
+            const int top = N - 1 - (i0 + j0);  // last plane with a volume node in the tile
+            for (int k0 = 1; k0 <= top; k0 += m.kseg) {
+              const int k1 = std::min(top, k0 + m.kseg - 1);
+              const long long key = m.korder == 1 ? k0 : -(long long)(k1 - k0 + 1);
+              its.push_back({key, make_int4(tile, k0, k1, 0)});
+            }
+          }
+        while (its.size() % 4) its.push_back({its.empty() ? 0 : its.back().first, make_int4(s << 20 | empty_tile, 1, 0, 0)});
+      }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (auto& p : its) by_class[cls].push_back(p.second);
+  }
+  D.h_items = by_class[0];
+  D.n_items_nc = (int)D.h_items.size();
+  D.h_items.insert(D.h_items.end(), by_class[1].begin(), by_class[1].end());
+  D.n_items = (int)D.h_items.size();
+}
+
 static void build_depth(Mesh& m, int d) {
   Depth& D = m.depth[d];
   const int nt = m.nt;
@@ -299,43 +357,7 @@ static void build_depth(Mesh& m, int d) {
     stencils_for(m, t, D.tet_level[t], &D.h_sten[(size_t)s * 16 * kNDir]);
     elements_for(m, t, D.tet_level[t], &D.h_elem[(size_t)s * 96]);
   }
-  // volume work list: tiles of kTI x kTJ (i0, j0), 4 per warp item, one tet
-  // per item; longest k-march first.
-  struct Tile {
-    int slot, i0, j0;
-  };
-  std::vector<std::vector<uint4>> items_by_class(2);
-  for (int cls = 0; cls < 2; ++cls) {
-    std::vector<std::pair<int, uint4>> its;  // (height, item)
-    for (int s = 0; s < ns; ++s) {
-      if ((s < D.n_slots_nc) != (cls == 0)) continue;
-      const int N = D.h_tets[s].N;
-      std::vector<Tile> tiles;
-      for (int j0 = 1; j0 <= N - 2; j0 += kTJ)
-        for (int i0 = 1; i0 + j0 <= N - 2; i0 += kTI) tiles.push_back({s, i0, j0});
-      std::stable_sort(tiles.begin(), tiles.end(),
-                       [](const Tile& a, const Tile& b) { return a.i0 + a.j0 < b.i0 + b.j0; });
-      for (size_t q = 0; q < tiles.size(); q += 4) {
-        unsigned w[4];
-        for (int g = 0; g < 4; ++g) {
-          if (q + g < tiles.size()) {
-            const Tile& tl = tiles[q + g];
-            w[g] = (unsigned)tl.slot << 20 | (unsigned)tl.j0 << 10 | (unsigned)tl.i0;
-          } else {
-            w[g] = (unsigned)s << 20 | 1023u << 10 | 1023u;  // empty tile (never valid)
-          }
-        }
-        const int height = N - 1 - (tiles[q].i0 + tiles[q].j0);
-        its.push_back({height, make_uint4(w[0], w[1], w[2], w[3])});
-      }
-    }
-    std::stable_sort(its.begin(), its.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (auto& p : its) items_by_class[cls].push_back(p.second);
-  }
-  D.h_items = items_by_class[0];
-  D.n_items_nc = (int)D.h_items.size();
-  D.h_items.insert(D.h_items.end(), items_by_class[1].begin(), items_by_class[1].end());
-  D.n_items = (int)D.h_items.size();
+  build_items(m, D);
   // rows (slot, j, k)
   D.h_rows.clear();
   for (int s = 0; s < ns; ++s) {
@@ -423,6 +445,31 @@ static void build_depth(Mesh& m, int d) {
       const BCopy& c = D.h_bcopies[q];
       D.h_mult[(size_t)c.slot * 16 + c.mask] = (unsigned char)(D.h_bstart[b + 1] - D.h_bstart[b]);
     }
+}
+
+template <class T>
+static T* reupload(Depth& d, T* old, const std::vector<T>& h) {
+  if (old) {
+    cudaFree(old);
+    d.allocations.erase(std::remove(d.allocations.begin(), d.allocations.end(), (void*)old), d.allocations.end());
+  }
+  return upload(d, h);
+}
+
+void set_kseg(Mesh& m, int kseg, int korder) {
+  HHG_REQUIRE(kseg >= 1 && kseg <= 1024, "kseg must be in [1, 1024]");
+  HHG_REQUIRE(korder >= 0 && korder <= 2, "korder must be 0, 1 or 2");
+  m.kseg = kseg;
+  m.korder = korder;
+  for (Depth& D : m.depth) {
+    build_items(m, D);
+    if (m.device) {
+      HHG_CUDA(cudaDeviceSynchronize());
+      D.dev.items = reupload(D, const_cast<int4*>(D.dev.items), D.h_items);
+      D.dev.n_items = D.n_items;
+      D.dev.n_items_nc = D.n_items_nc;
+    }
+  }
 }
 
 static void upload_depth(Depth& D) {
@@ -568,6 +615,7 @@ Mesh* build_mesh(const double* verts, int nv, const int* tets, int nt, const int
     m->d_red = static_cast<double*>(dalloc(D0, 4096 * sizeof(double)));
     m->d_counter = static_cast<unsigned*>(dalloc(D0, 64 * sizeof(unsigned)));
     HHG_CUDA(cudaMemset(m->d_counter, 0, 64 * sizeof(unsigned)));
+    m->d_error = m->d_counter + 32;
     m->d_scalars = static_cast<double*>(dalloc(D0, 64 * sizeof(double)));
     HHG_CUDA(cudaMemset(m->d_scalars, 0, 64 * sizeof(double)));
     HHG_CUDA(cudaMallocHost(&m->h_pinned, 64 * sizeof(double)));

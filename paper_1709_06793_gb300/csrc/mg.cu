@@ -75,7 +75,7 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
       D.k64 = static_cast<double*>(dalloc(D, n * 8));
       D.k16d = static_cast<double*>(dalloc(D, n * 8));
       D.k32 = static_cast<float*>(dalloc(D, n * 4));
-      D.k16 = static_cast<__nv_bfloat16*>(dalloc(D, n * 2));
+      D.k16 = static_cast<__nv_bfloat16*>(dalloc(D, n * 2 + 16));  // +16: staged as 4-byte words
     }
   }
   Depth& D0 = m.depth[0];

@@ -65,6 +65,9 @@ def _load():
         "hhg_lambda_max": [P, I, I, I, C.POINTER(D), P],
         "hhg_dot": [P, I, P, P, I, C.POINTER(D), P],
         "hhg_solve": [P, C.POINTER(SolveParams), P, P, C.POINTER(SolveStats), P],
+        "hhg_set_option": [P, C.c_char_p, D],
+        "hhg_device_status": [P],
+        "hhg_get_option": [P, C.c_char_p, C.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -213,6 +216,20 @@ def hhg_solve(mesh, f, u, tol=1e-8, maxit=200, mode=HHG_SOLVE_FP64, smoother=HHG
         _check(code)
     return {"iterations": st.iterations, "outer": st.outer, "rel_residual": st.rel_residual,
             "time_ms": st.time_ms, "status": STATUS.get(code, code)}
+
+
+def hhg_device_status(mesh):
+    _check(_lib.hhg_device_status(mesh))
+
+
+def hhg_set_option(mesh, key, value):
+    _check(_lib.hhg_set_option(mesh, key.encode(), float(value)))
+
+
+def hhg_get_option(mesh, key):
+    out = C.c_double()
+    _check(_lib.hhg_get_option(mesh, key.encode(), C.byref(out)))
+    return out.value
 
 
 class Mesh:
