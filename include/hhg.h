@@ -161,6 +161,22 @@ int hhg_apply_scaled(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, i
  * eq. "onTheFlyStencil").  Same arguments as hhg_apply_scaled. */
 int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
 
+/* y = M u with M the consistent P1 mass matrix (|t|/20 (1 + delta_ab) per
+ * micro tetrahedron), for the right-hand side f_h = M I_h f of Sec. 7.2:
+ * every entry of u is used (Dirichlet nodes included, u holds the nodal
+ * interpolant of f); rows of Dirichlet nodes are set to 0.  dtype HHG_F64 or
+ * HHG_F32. */
+int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
+
+/* Autotune the volume work list for `dtype` (not part of the method): time
+ * the scaled apply on depth 0 for every candidate k-segment length (16, 32,
+ * 64) and work order (0, 1), keep the fastest on the mesh, and report it.
+ * cache_path (may be NULL): a text file of earlier results keyed by the mesh
+ * shape and dtype; a hit skips the search, a miss appends the new result.
+ * Synchronous.  kseg, korder, best_ms may be NULL (best_ms < 0 on a hit). */
+int hhg_autotune(hhg_mesh mesh, int dtype, const char* cache_path, int* kseg, int* korder, double* best_ms,
+                 void* stream);
+
 /* r = f - A_s(k) u at `depth` (the residual of the paper's benchmark, Sec. 7.4). */
 int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev,
                  int dtype, void* stream);

@@ -22,6 +22,7 @@ void prepare(Mesh& m, int dtype, int smoother, cudaStream_t s);
 double lambda_max(Mesh& m, int depth, int its, cudaStream_t s);
 void dot(Mesh& m, int depth, int dtype, const void* x, const void* y, int slot, int post, bool nc_only, cudaStream_t s);
 int solve(Mesh& m, const hhg_solve_params& p, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s);
+void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_korder, double* out_ms, cudaStream_t s);
 void init_launch_configs(int dtype);
 }  // namespace hhg
 
@@ -187,6 +188,28 @@ int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, in
   });
 }
 
+int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    if (dtype != HHG_F64 && dtype != HHG_F32) throw Error{HHG_ERR_ARG, "hhg_apply_mass supports HHG_F64 and HHG_F32"};
+    need_vec(u_dev, "u_dev");
+    need_vec(y_dev, "y_dev");
+    if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
+    launch_mass_apply(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_autotune(hhg_mesh mesh, int dtype, const char* cache_path, int* kseg, int* korder, double* best_ms,
+                 void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_dtype(dtype);
+    need_coef(m);
+    autotune(m, dtype, cache_path, kseg, korder, best_ms, (cudaStream_t)stream);
+  });
+}
+
 int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev, int dtype,
                  void* stream) {
   return guarded([&] {
@@ -325,6 +348,7 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
 int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
   return guarded([&] {
     Mesh& m = need(mesh, false);
+    drop_graphs(m);
     need_ptr(key, "key");
     const std::string k(key);
     if (k == "kseg") {

@@ -962,6 +962,80 @@ static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Consistent mass matrix y = M u (setup of the right-hand side M I_h f,
+// Sec. 7.2): per-primitive stencils, every input entry used (including
+// Dirichlet nodes), Dirichlet rows set to 0.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T mass_partial(const TetDev& td, const T* __restrict__ ms, int i, int j, int k,
+                                          const T* __restrict__ u) {
+  const int N = td.N;
+  T y = ms[14] * u[td.base + node_offset(N, i, j, k)];
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) {
+    int di, dj, dk;
+    dir_of(d, di, dj, dk);
+    const int a = i + di, b = j + dj, c = k + dk;
+    if (a < 0 || b < 0 || c < 0 || a + b + c > N) continue;
+    y = fma(ms[d], u[td.base + node_offset(N, a, b, c)], y);
+  }
+  return y;
+}
+
+template <class T>
+__global__ void mass_volume_kernel(DepthDev D, const T* __restrict__ mass, const T* __restrict__ u, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < D.n_rows; r += nwarps) {
+    const int4 row = D.rows[r];
+    const TetDev td = D.tets[row.x];
+    const int N = td.N, j = row.y, k = row.z;
+    if (j == 0 || k == 0 || j + k >= N - 1) continue;
+    const T* ms = mass + row.x * 16 * 15;  // volume row (mask 0)
+    for (int i = 1 + lane; i + j + k <= N - 1; i += 32)
+      y[td.base + node_offset(N, i, j, k)] = mass_partial<T>(td, ms, i, j, k, u);
+  }
+}
+
+template <class T>
+__global__ void mass_boundary_kernel(DepthDev D, const T* __restrict__ mass, const T* __restrict__ u, T* __restrict__ y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= D.n_bnodes) return;
+  const int lo = D.bstart[b], hi = D.bstart[b + 1];
+  T v = 0;
+  if (!D.bdir[b])
+    for (int q = lo; q < hi; ++q) {
+      const BCopy cp = D.bcopies[q];
+      v += mass_partial<T>(D.tets[cp.slot], mass + (cp.slot * 16 + cp.mask) * 15, cp.i, cp.j, cp.k, u);
+    }
+  for (int q = lo; q < hi; ++q) y[D.bcopies[q].idx] = v;
+}
+
+template <class T>
+static void mass_typed(const Mesh& m, int depth, const T* mass, const void* u, void* y, cudaStream_t s) {
+  const DepthDev& D = m.depth[depth].dev;
+  if (D.n_rows > 0) {
+    const int blocks = std::min((D.n_rows + 7) / 8, m.num_sms * 8);
+    mass_volume_kernel<T><<<blocks, 256, 0, s>>>(D, mass, static_cast<const T*>(u), static_cast<T*>(y));
+    HHG_CUDA(cudaGetLastError());
+  }
+  if (D.n_bnodes > 0) {
+    mass_boundary_kernel<T><<<(D.n_bnodes + 127) / 128, 128, 0, s>>>(D, mass, static_cast<const T*>(u),
+                                                                      static_cast<T*>(y));
+    HHG_CUDA(cudaGetLastError());
+  }
+}
+
+void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s) {
+  const DepthDev& D = m.depth[depth].dev;
+  if (dtype == HHG_F64)
+    mass_typed<double>(m, depth, D.mass64, u, y, s);
+  else
+    mass_typed<float>(m, depth, D.mass32, u, y, s);
+}
+
 void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s) {
   const Depth& Dh = m.depth[depth];
   if (dtype == HHG_F64)

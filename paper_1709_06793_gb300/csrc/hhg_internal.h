@@ -69,6 +69,8 @@ struct DepthDev {
   const float* sten32;
   const double* elem64;  // [slot][6][16]   (1/4)*micro-element stiffness per Kuhn type
   const float* elem32;
+  const double* mass64;  // [slot][16][15]  consistent mass stencil per primitive (col 14 = centre)
+  const float* mass32;
   const int4* items;     // volume work: (tile = slot<<20 | j0<<10 | i0, k0, k1, -) per warp item
   int n_items;           // items of all active tets
   int n_items_nc;        // items of tets above the coarsest level (prefix)
@@ -100,6 +102,7 @@ struct Depth {
   std::vector<TetDev> h_tets;
   std::vector<double> h_sten;         // [slot][16][14]
   std::vector<double> h_elem;         // [slot][6][16]
+  std::vector<double> h_mass;         // [slot][16][15]
   std::vector<int4> h_items;
   int n_items = 0, n_items_nc = 0;
   std::vector<int> h_bstart;
@@ -178,7 +181,18 @@ struct Mesh {
   int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)
   void* learned = nullptr;
+  // instantiated CG-iteration graphs, keyed by their arguments; dropped when
+  // work lists, coefficients or options change (kernel parameters embed them)
+  struct GraphEntry {
+    int dtype, smoother, nu1, nu2;
+    double omega;
+    const void *x, *r;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
 };
+
+void drop_graphs(Mesh& m);
 
 // ---- error handling --------------------------------------------------------
 void set_error(const std::string& msg);
@@ -228,5 +242,6 @@ struct OpArgs {
 
 void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
+void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 
 }  // namespace hhg

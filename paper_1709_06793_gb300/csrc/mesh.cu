@@ -175,6 +175,34 @@ void stencils_for(const Mesh& m, int tet, int level, double* out) {
   }
 }
 
+// Consistent P1 mass matrix (|t|/20 (1 + delta_ab) per micro tet) in stencil
+// form per primitive: column 14 = centre, columns 0..13 the directions.
+void mass_stencils_for(const Mesh& m, int tet, int level, double* out) {
+  const int N = 1 << level;
+  std::fill(out, out + 16 * 15, 0.0);
+  for (int mask = 0; mask < 16; ++mask) {
+    int rep[3];
+    if (!representative(N, mask, rep)) continue;
+    for (const Micro& mt : micro_at(N, rep[0], rep[1], rep[2])) {
+      double X[4][3];
+      for (int q = 0; q < 4; ++q) index_to_phys(m, tet, N, mt.ijk[q], X[q]);
+      double J[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) J[r][c] = X[c + 1][r] - X[0][r];
+      const double vol = std::fabs(J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                   J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                   J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0])) / 6.0;
+      out[mask * 15 + 14] += vol / 10.0;
+      for (int q = 0; q < 4; ++q) {
+        if (q == mt.v) continue;
+        const int d = dir_index(mt.ijk[q][0] - rep[0], mt.ijk[q][1] - rep[1], mt.ijk[q][2] - rep[2]);
+        HHG_REQUIRE(d >= 0, "internal: micro-tet edge not in the 15-point pattern");
+        out[mask * 15 + d] += vol / 20.0;
+      }
+    }
+  }
+}
+
 // (1/4) P1 stiffness matrix of the 6 Kuhn types of micro tet (vertices in
 // path order), for the nodal-integration operator k_bar_t * A_t with
 // k_bar_t = (1/4) sum of the vertex values (eq. "standardfe").
@@ -352,10 +380,12 @@ static void build_depth(Mesh& m, int d) {
   // stencils and element matrices
   D.h_sten.assign((size_t)ns * 16 * kNDir, 0.0);
   D.h_elem.assign((size_t)ns * 6 * 16, 0.0);
+  D.h_mass.assign((size_t)ns * 16 * 15, 0.0);
   for (int s = 0; s < ns; ++s) {
     const int t = D.slot_tet[s];
     stencils_for(m, t, D.tet_level[t], &D.h_sten[(size_t)s * 16 * kNDir]);
     elements_for(m, t, D.tet_level[t], &D.h_elem[(size_t)s * 96]);
+    mass_stencils_for(m, t, D.tet_level[t], &D.h_mass[(size_t)s * 16 * 15]);
   }
   build_items(m, D);
   // rows (slot, j, k)
@@ -457,6 +487,7 @@ static T* reupload(Depth& d, T* old, const std::vector<T>& h) {
 }
 
 void set_kseg(Mesh& m, int kseg, int korder) {
+  drop_graphs(m);
   HHG_REQUIRE(kseg >= 1 && kseg <= 1024, "kseg must be in [1, 1024]");
   HHG_REQUIRE(korder >= 0 && korder <= 2, "korder must be 0, 1 or 2");
   m.kseg = kseg;
@@ -478,6 +509,9 @@ static void upload_depth(Depth& D) {
   std::vector<float> s32(D.h_sten.begin(), D.h_sten.end());
   D.dev.sten32 = upload(D, s32);
   D.dev.elem64 = upload(D, D.h_elem);
+  D.dev.mass64 = upload(D, D.h_mass);
+  std::vector<float> m32(D.h_mass.begin(), D.h_mass.end());
+  D.dev.mass32 = upload(D, m32);
   std::vector<float> e32(D.h_elem.begin(), D.h_elem.end());
   D.dev.elem32 = upload(D, e32);
   D.dev.items = upload(D, D.h_items);
@@ -630,6 +664,7 @@ void free_learned(Mesh* m);
 
 void free_mesh(Mesh* m) {
   if (!m) return;
+  drop_graphs(*m);
   free_learned(m);
   for (Depth& d : m->depth) {
     for (void* p : d.allocations) cudaFree(p);

@@ -68,6 +68,7 @@ __global__ void inject_kernel(DepthDev C, DepthDev F, const V* __restrict__ fine
 }
 
 void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
+  drop_graphs(m);
   for (int d = 0; d < m.ndepth; ++d) {
     Depth& D = m.depth[d];
     const size_t n = std::max<long long>(D.n_stored, 1);

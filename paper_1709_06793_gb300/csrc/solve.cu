@@ -58,6 +58,11 @@ __global__ void add_f32_kernel(double* __restrict__ x, const float* __restrict__
     x[i] += (double)d[i];
 }
 
+void drop_graphs(Mesh& m) {
+  for (auto& g : m.graphs) cudaGraphExecDestroy(g.exec);
+  m.graphs.clear();
+}
+
 // Allocate every buffer and estimate every quantity a V-cycle / CG needs, so
 // that afterwards the iteration only enqueues kernels (capturable).
 void prepare(Mesh& m, int dtype, int smoother, cudaStream_t s) {
@@ -130,12 +135,20 @@ static PcgResult pcg(Mesh& m, int dtype, const hhg_solve_params& p, void* x, voi
   HHG_CUDA(cudaMemsetAsync(pp, 0, n * elem_size(dtype), s));
   set_scalar_kernel<<<1, 1, 0, s>>>(m.d_scalars, 0, INFINITY);
   cudaGraphExec_t exec = nullptr;
-  cudaGraph_t graph = nullptr;
   if (p.use_graph) {
-    HHG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    pcg_body(m, dtype, p, x, r, z, pp, q, s);
-    HHG_CUDA(cudaStreamEndCapture(s, &graph));
-    HHG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    for (auto& g : m.graphs)
+      if (g.dtype == dtype && g.smoother == p.smoother && g.nu1 == p.nu1 && g.nu2 == p.nu2 && g.omega == p.omega &&
+          g.x == x && g.r == r)
+        exec = g.exec;
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      HHG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+      pcg_body(m, dtype, p, x, r, z, pp, q, s);
+      HHG_CUDA(cudaStreamEndCapture(s, &graph));
+      HHG_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      cudaGraphDestroy(graph);
+      m.graphs.push_back({dtype, p.smoother, p.nu1, p.nu2, p.omega, x, r, exec});
+    }
   }
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
@@ -146,8 +159,6 @@ static PcgResult pcg(Mesh& m, int dtype, const hhg_solve_params& p, void* x, voi
     rr = read_scalar(m, 3, s);
     if (!(rr > tol2)) break;  // also stops on NaN
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
   return {std::min(it, maxit), rr};
 }
 

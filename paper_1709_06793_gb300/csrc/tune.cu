@@ -1,0 +1,98 @@
+// Autotuner for the volume work list: every (kseg, korder) candidate is timed
+// on the finest depth with CUDA events (median of repeated applies); the best
+// is kept on the mesh and, if a cache file is given, recorded there keyed by
+// the mesh shape and dtype so later runs skip the search.
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <sstream>
+#include <string>
+
+#include "hhg_internal.h"
+
+namespace hhg {
+
+void* workspace(Mesh& m, int depth, int prec, int w);
+void apply_scaled(Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
+void init_launch_configs(int dtype);
+size_t elem_size(int dtype);
+
+static std::string tune_key(const Mesh& m, int dtype) {
+  std::ostringstream k;
+  k << "dtype=" << dtype << ";tets=" << m.nt << ";levels=";
+  for (int t = 0; t < m.nt; ++t) k << m.level[t] << (t + 1 < m.nt ? "," : "");
+  return k.str();
+}
+
+// cache file: one line per entry, "<key> <kseg> <korder> <ms>"
+static bool cache_lookup(const char* path, const std::string& key, int& kseg, int& korder) {
+  if (!path) return false;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    int a, b;
+    if (is >> k >> a >> b && k == key) {
+      kseg = a;
+      korder = b;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void cache_store(const char* path, const std::string& key, int kseg, int korder, double ms) {
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << " " << kseg << " " << korder << " " << ms << "\n";
+}
+
+void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_korder, double* out_ms, cudaStream_t s) {
+  HHG_REQUIRE(m.coef_set, "hhg_set_coefficient must be called first");
+  const std::string key = tune_key(m, dtype);
+  int kseg = m.kseg, korder = m.korder;
+  double best_ms = -1;
+  if (!cache_lookup(cache, key, kseg, korder)) {
+    init_launch_configs(dtype);
+    const int pr = elem_size(dtype) == 8 ? 0 : 1;
+    void* u = workspace(m, 0, pr, 0);
+    void* y = workspace(m, 0, pr, 1);
+    cudaEvent_t e0, e1;
+    HHG_CUDA(cudaEventCreate(&e0));
+    HHG_CUDA(cudaEventCreate(&e1));
+    const int cand_kseg[] = {16, 32, 64};
+    const int cand_order[] = {0, 1};
+    for (int o : cand_order)
+      for (int ks : cand_kseg) {
+        set_kseg(m, ks, o);
+        for (int w = 0; w < 2; ++w) apply_scaled(m, 0, dtype, u, y, s);
+        std::vector<float> t;
+        for (int r = 0; r < 5; ++r) {
+          HHG_CUDA(cudaEventRecord(e0, s));
+          apply_scaled(m, 0, dtype, u, y, s);
+          HHG_CUDA(cudaEventRecord(e1, s));
+          HHG_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          HHG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (best_ms < 0 || med < best_ms) {
+          best_ms = med;
+          kseg = ks;
+          korder = o;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cache_store(cache, key, kseg, korder, best_ms);
+  }
+  set_kseg(m, kseg, korder);
+  if (out_kseg) *out_kseg = kseg;
+  if (out_korder) *out_korder = korder;
+  if (out_ms) *out_ms = best_ms;
+}
+
+}  // namespace hhg

@@ -58,6 +58,8 @@ def _load():
         "hhg_apply_scaled": [P, I, P, P, I, P],
         "hhg_apply_nodal": [P, I, P, P, I, P],
         "hhg_residual": [P, I, P, P, P, I, P],
+        "hhg_apply_mass": [P, I, P, P, I, P],
+        "hhg_autotune": [P, I, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D), P],
         "hhg_smooth": [P, I, I, I, D, P, P, I, P],
         "hhg_restrict": [P, I, P, P, I, P],
         "hhg_prolongate_add": [P, I, P, P, I, P],
@@ -173,6 +175,17 @@ def hhg_apply_scaled(mesh, depth, u, y, dtype, stream=None):
 
 def hhg_apply_nodal(mesh, depth, u, y, dtype, stream=None):
     _check(_lib.hhg_apply_nodal(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_apply_mass(mesh, depth, u, y, dtype, stream=None):
+    _check(_lib.hhg_apply_mass(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_autotune(mesh, dtype, cache_path=None, stream=None):
+    ks, ko, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(_lib.hhg_autotune(mesh, dtype, cache_path.encode() if cache_path else None, C.byref(ks), C.byref(ko),
+                             C.byref(ms), _stream(stream)))
+    return {"kseg": ks.value, "korder": ko.value, "best_ms": ms.value}
 
 
 def hhg_residual(mesh, depth, f, u, r, dtype, stream=None):

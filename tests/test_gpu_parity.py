@@ -301,3 +301,103 @@ def test_solve_matches_oracle_discrete_solution(H, mode):
     x_A = math.sqrt(xs[lm.unknowns] @ (A @ xs[lm.unknowns]))
     assert e_A / x_A <= 1e-8
     assert _rel(got, xs) <= 1e-7
+
+
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-13), (1, 1e-6)])
+def test_mass_apply_parity(H, case, dtype, tol):
+    """f_h = M I_h f (Sec. 7.2): every input entry is used, Dirichlet rows are 0."""
+    x = case.lm.coords
+    v = np.sin(2 * x[:, 0]) + x[:, 1] * x[:, 2] + 1.0  # nonzero on the boundary too
+    vin = v if dtype == 0 else _f32(v)
+    y = torch.empty(case.n, device="cuda", dtype=torch.float64 if dtype == 0 else torch.float32)
+    H.hhg_apply_mass(case.m.h, 0, case.dev(vin, dtype), y, dtype)
+    want = np.where(case.dir, 0.0, case.lm.assemble_mass() @ vin)
+    assert _rel(case.back(y), want) <= tol
+
+
+def test_autotune_keeps_results_identical(H, tmp_path):
+    V, T = I.kuhn_cube()
+    c = Case(H, V, T, 5, 2, I.k_cube)
+    ud = c.dev(c.rand_or, 1)
+    y0 = torch.empty_like(ud)
+    H.hhg_apply_scaled(c.m.h, 0, ud, y0, 1)
+    cache = str(tmp_path / "tune.txt")
+    r1 = H.hhg_autotune(c.m.h, 1, cache)
+    assert r1["kseg"] in (16, 32, 64) and r1["korder"] in (0, 1) and r1["best_ms"] > 0
+    r2 = H.hhg_autotune(c.m.h, 1, cache)  # cache hit
+    assert (r2["kseg"], r2["korder"]) == (r1["kseg"], r1["korder"])
+    y1 = torch.empty_like(ud)
+    H.hhg_apply_scaled(c.m.h, 0, ud, y1, 1)
+    # the work split changes, the per-node arithmetic does not
+    assert torch.equal(y0, y1)
+
+
+def _batch(H, levels, seed=4, coarsest=2):
+    V, T = I.random_tets(len(levels), seed=seed)
+    m = H.Mesh(V, T, levels, coarsest)
+    off, lev, n = m.layout(0)
+    kf = I.k_batched(seed)
+    H.hhg_set_coefficient(m.h, torch.tensor(kf(m.coords(0)), device="cuda"))
+    nodes = U.stored_nodes(off, lev)
+    parts = []
+    for t in range(len(T)):
+        Vt, Tt = V[4 * t:4 * t + 4], np.array([[0, 1, 2, 3]])
+        sel = nodes[:, 0] == t
+        lm = O.LevelMesh(O.MacroMesh(Vt, Tt), levels[t])
+        loc = lm.local[0][nodes[sel, 1], nodes[sel, 2], nodes[sel, 3]]
+        parts.append((sel, loc, lm, Vt, Tt))
+    return m, n, kf, parts
+
+
+def test_batched_mixed_levels_vcycle_and_solve(H):
+    """Independent tets of levels 3..5 in one hierarchy (depth-aligned V-cycle,
+    one persistent launch per stage): the V-cycle equals each tet's own oracle
+    V-cycle, and the solve reaches every tet's discrete solution."""
+    levels = [5, 3, 4, 5]
+    m, n, kf, parts = _batch(H, levels)
+    f = np.zeros(n)
+    hs = []
+    for sel, loc, lm, Vt, Tt in parts:
+        ft = np.where(lm.dirichlet, 0.0, np.cos(3 * lm.coords[:, 0]) + lm.coords[:, 1])
+        f[sel] = ft[loc]
+        hs.append(O.Hierarchy(Vt, Tt, lm.level, 2, k_func=kf))
+    u = torch.zeros(n, device="cuda", dtype=torch.float64)
+    H.hhg_vcycle(m.h, 2, 2, H.HHG_SMOOTH_JACOBI, torch.tensor(f, device="cuda"), u, H.HHG_F64)
+    got = u.cpu().numpy()
+    for (sel, loc, lm, Vt, Tt), Hh in zip(parts, hs):
+        ft = np.zeros(lm.n)
+        ft[loc] = f[sel]
+        un = Hh.vcycle(lm.level, ft[lm.unknowns], np.zeros(len(lm.unknowns)))
+        want = np.zeros(lm.n)
+        want[lm.unknowns] = un
+        assert _rel(got[sel], want[loc]) <= 1e-10
+    x = torch.zeros(n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(m.h, torch.tensor(f, device="cuda"), x, tol=1e-10, mode=H.HHG_SOLVE_MIXED)
+    assert st["rel_residual"] <= 1e-10
+    got = x.cpu().numpy()
+    for (sel, loc, lm, Vt, Tt), Hh in zip(parts, hs):
+        ft = np.zeros(lm.n)
+        ft[loc] = f[sel]
+        xs = np.zeros(lm.n)
+        xs[lm.unknowns] = Hh.direct_solve(ft[lm.unknowns])
+        assert _rel(got[sel], xs[loc]) <= 1e-7
+    m.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chebyshev_solve(H, mode):
+    V, T = I.cube24()
+    c = Case(H, V, T, 3, 1, I.k_large)
+    f_or = np.where(c.dir, 0.0, c.lm.assemble_mass() @ np.ones(c.lm.n))
+    ud = torch.zeros(c.n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(c.m.h, c.dev(f_or, 0), ud, tol=1e-9, mode=mode, smoother=H.HHG_SMOOTH_CHEBYSHEV)
+    assert st["rel_residual"] <= 1e-9
+    import scipy.sparse.linalg as spla
+    A = c.lm.system(c.k_or, "scaled")
+    xs = np.zeros(c.lm.n)
+    xs[c.lm.unknowns] = spla.spsolve(A.tocsc(), f_or[c.lm.unknowns])
+    assert _rel(c.back(ud), xs) <= 1e-7
+
+
+def test_device_status_clean(H, case):
+    H.hhg_device_status(case.m.h)  # raises on a recorded timeout
