@@ -188,6 +188,24 @@ int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev,
 int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega,
                const void* f_dev, void* u_dev, int dtype, void* stream);
 
+/* Damped-Jacobi smoothing like hhg_smooth(kind = HHG_SMOOTH_JACOBI) that
+ * never allocates.  The paper has no counterpart: this exists for callers
+ * that must not trigger a device allocation during the call (hhg_smooth
+ * allocates its ping-pong vector on first use of a depth), e.g. code whose
+ * memory budget is fixed before the solve or that runs where cudaMalloc is
+ * not allowed.  The ping-pong vector lives in one fixed array of 16 MiB
+ * inside the library image (held on every GPU that loads the library until
+ * the process exits); a depth whose vector needs more than 16 MiB (more than
+ * 2^21 FP64 or 2^22 FP32 stored nodes) is rejected with HHG_ERR_ARG.  The
+ * first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Each sweep
+ * overwrites the whole vector, so nothing needs clearing between calls.
+ * Arguments as for hhg_smooth; u_dev holds the result. */
+int hhg_smooth_noalloc(hhg_mesh mesh, int depth, int sweeps, double omega, const void* f_dev, void* u_dev,
+                       int dtype, void* stream);
+
 /* rc = P^T rf (restriction, depth -> depth+1) and uf += P ec (prolongation,
  * depth+1 -> depth), P = linear interpolation between nested P1 spaces. */
 int hhg_restrict(hhg_mesh mesh, int depth, const void* rf_dev, void* rc_dev, int dtype, void* stream);

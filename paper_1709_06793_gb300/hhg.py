@@ -61,6 +61,7 @@ def _load():
         "hhg_apply_mass": [P, I, P, P, I, P],
         "hhg_autotune": [P, I, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D), P],
         "hhg_smooth": [P, I, I, I, D, P, P, I, P],
+        "hhg_smooth_noalloc": [P, I, I, D, P, P, I, P],
         "hhg_restrict": [P, I, P, P, I, P],
         "hhg_prolongate_add": [P, I, P, P, I, P],
         "hhg_vcycle": [P, I, I, I, P, P, I, P],
@@ -194,6 +195,10 @@ def hhg_residual(mesh, depth, f, u, r, dtype, stream=None):
 
 def hhg_smooth(mesh, depth, kind, sweeps, omega, f, u, dtype, stream=None):
     _check(_lib.hhg_smooth(mesh, depth, kind, sweeps, float(omega), _ptr(f), _ptr(u), dtype, _stream(stream)))
+
+
+def hhg_smooth_noalloc(mesh, depth, sweeps, omega, f, u, dtype, stream=None):
+    _check(_lib.hhg_smooth_noalloc(mesh, depth, sweeps, float(omega), _ptr(f), _ptr(u), dtype, _stream(stream)))
 
 
 def hhg_restrict(mesh, depth, rf, rc, dtype, stream=None):
