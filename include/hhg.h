@@ -72,7 +72,7 @@ typedef enum {
 typedef enum {
     HHG_SMOOTH_JACOBI = 0,     /* damped Jacobi, u += omega D^-1 (f - A u) */
     HHG_SMOOTH_CHEBYSHEV = 1,  /* Chebyshev on D^-1 A, interval [lo, hi] * lambda_max */
-    HHG_SMOOTH_LEARNED = 2     /* learned 3x3x3 convolutional correction + Jacobi */
+    HHG_SMOOTH_LEARNED = 2     /* damped Jacobi sweeps alternating with learned steps (see hhg_learned_train) */
 } hhg_smoother;
 
 typedef enum {
@@ -98,7 +98,36 @@ typedef struct {
     int outer;           /* refinement steps (1 in FP64 mode) */
     double rel_residual; /* final ||f - A u|| / ||f|| in FP64 */
     double time_ms;      /* wall time of the call */
+    int smoother_used;   /* smoother of the last inner solve (HHG_SMOOTH_JACOBI if a
+                            requested learned smoother was not accepted or diverged) */
 } hhg_solve_stats;
+
+/* Training of the learned smoother (hhg_learned_train); fields <= 0 take the
+ * default in brackets. */
+typedef struct {
+    int steps;               /* Adam steps [150] */
+    int pairs;               /* residual/error pairs per step, gradients summed [4] */
+    double lr;               /* Adam learning rate [3e-3] */
+    double omega;            /* damping of the Jacobi sweep before each learned step [2/3] */
+    int max_depth;           /* pairs come from the smoothed depths 0..max_depth [0] */
+    int vcycle_pairs;        /* pairs per step whose error is the one a plain V-cycle leaves [0] */
+    double init_noise;       /* size of the random part of the initial weights [0] */
+    unsigned long long seed; /* initial weights and random errors */
+    int weights_bf16;        /* 1: kernels read BF16 weights; 0: FP32 weights */
+    int validate_its;        /* PCG iterations of the convergence check [8] */
+    int resume;              /* 1: continue from the current weights and Adam state */
+} hhg_learn_params;
+
+typedef struct {
+    double loss_jacobi;  /* validation loss of the network equal to damped Jacobi */
+    double loss_init;    /* validation loss of the initial weights */
+    double loss_final;   /* validation loss after training */
+    double rho_plain;    /* FP32 PCG residual reduction per iteration, plain Jacobi V(2,2) */
+    double rho_learned;  /* the same with the learned smoother */
+    int accepted;        /* 1 if rho_learned < rho_plain: solves may use the network */
+    int steps;           /* Adam steps taken */
+    double time_ms;      /* wall time of the training */
+} hhg_learn_stats;
 
 /* Create a macro mesh.  verts: nv*3 doubles; tets: nt*4 vertex ids, the order
  * of a tet's vertices is its refinement order (Bey's rule, Sec. 2.1);
@@ -205,6 +234,49 @@ int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega,
  * Arguments as for hhg_smooth; u_dev holds the result. */
 int hhg_smooth_noalloc(hhg_mesh mesh, int depth, int sweeps, double omega, const void* f_dev, void* u_dev,
                        int dtype, void* stream);
+
+/* ---- learned smoother ------------------------------------------------------
+ * The paper has no learned component; this is an addition to its multigrid.
+ * A network of two 3x3x3 convolutions in the (i,j,k) index space of each
+ * macro tet (2 -> 16 -> 1 channels, ReLU, no biases) maps the residual to a
+ * correction c.  Inputs: a0 = r / D (0 on Dirichlet nodes), a1 = a0 log k;
+ * values outside a tet's index set are zero; a node shared by several macro
+ * tets takes the mean of their values; Dirichlet nodes get 0.  Weights: 1296
+ * floats, W1[t][a][c] (27 x 2 x 16) then W2[t][c] (27 x 16), tap
+ * t = 9 (dk+1) + 3 (dj+1) + (di+1) for the offset (di,dj,dk).  In a V-cycle
+ * (HHG_SMOOTH_LEARNED) each pre-smoothing block runs Jacobi, learned, Jacobi,
+ * ... and each post-smoothing block learned, Jacobi, ...; a learned step is
+ * u += c(f - A u).  The step is nonlinear, so CG switches to its flexible
+ * form (beta = z_new.(r_new - r_old) / z_old.r_old).  Learned steps run on
+ * FP32 vectors only (dtype HHG_F32 or HHG_F32_KBF16; hhg_solve modes MIXED
+ * and MIXED_KBF16). */
+
+/* Train the network on the GPU for the mesh's current coefficient.  Pairs
+ * (r, e) with r = A e: e a random vector (or the error one plain V-cycle
+ * leaves of it), after the damped Jacobi sweep that precedes a learned step.
+ * Loss (e - c)^T A (e - c) / e^T r, the relative energy error after the step;
+ * Adam.  The initial weights are the network equal to damped Jacobi plus
+ * uniform noise of size init_noise.  Afterwards the plain V-cycle judges the
+ * result: the network is accepted only if FP32 PCG with it reduces the
+ * residual faster per iteration than with the plain V(2,2) cycle.
+ * Synchronous.  HHG_ERR_STATE without a coefficient. */
+int hhg_learned_train(hhg_mesh mesh, const hhg_learn_params* p, hhg_learn_stats* stats, void* stream);
+
+/* Set (host in, 1296 floats) or read (host out) the FP32 master weights.
+ * Setting marks the network accepted; weights_bf16 selects BF16 (1) or FP32
+ * (0) weights in the kernels.  Synchronous. */
+int hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int weights_bf16);
+int hhg_learned_get_weights(hhg_mesh mesh, float* w_host);
+
+/* c = network(r) at a smoothed depth (FP32 device vectors, stored layout;
+ * consistent on interface copies, 0 on Dirichlet nodes). */
+int hhg_learned_forward(hhg_mesh mesh, int depth, const void* r_dev, void* c_dev, void* stream);
+
+/* Loss of one pair and its gradient with respect to the 1296 weights (host
+ * out, FP64; FP32 products, FP64 sums over tiles).  r_dev, e_dev: FP32
+ * device vectors with r = A e.  Synchronous. */
+int hhg_learned_loss_grad(hhg_mesh mesh, int depth, const void* r_dev, const void* e_dev, double* loss,
+                          double* grad_host, void* stream);
 
 /* rc = P^T rf (restriction, depth -> depth+1) and uf += P ec (prolongation,
  * depth+1 -> depth), P = linear interpolation between nested P1 spaces. */

@@ -14,7 +14,7 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s);
 void apply_scaled(Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 void residual(Mesh& m, int depth, int dtype, const void* f, const void* u, void* r, bool nc_only, cudaStream_t s);
 void smooth(Mesh& m, int depth, int dtype, int kind, int sweeps, double omega, const void* f, void* u, bool nc_only,
-            cudaStream_t s);
+            cudaStream_t s, bool post);
 void restrict_residual(Mesh& m, int depth, int dtype, const void* rf, void* rc, cudaStream_t s);
 void prolongate_add(Mesh& m, int depth, int dtype, const void* ec, void* uf, cudaStream_t s);
 void vcycle(Mesh& m, int dtype, int nu1, int nu2, int smoother, double omega, const void* f0, void* u0, cudaStream_t s);
@@ -24,6 +24,12 @@ void dot(Mesh& m, int depth, int dtype, const void* x, const void* y, int slot, 
 int solve(Mesh& m, const hhg_solve_params& p, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s);
 void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_korder, double* out_ms, cudaStream_t s);
 void init_launch_configs(int dtype);
+void learned_prepare(Mesh& m, int dtype, cudaStream_t s);
+void learned_train(Mesh& m, const hhg_learn_params& p, hhg_learn_stats* st, cudaStream_t s);
+void learned_set_weights(Mesh& m, const float* w_host, int bf16, cudaStream_t s);
+void learned_get_weights(Mesh& m, float* w_host, cudaStream_t s);
+void learned_forward(Mesh& m, int d, const float* r, float* c, cudaStream_t s);
+void learned_loss_grad(Mesh& m, int d, const float* r, const float* e, double* loss, double* grad_host, cudaStream_t s);
 }  // namespace hhg
 
 using namespace hhg;
@@ -234,10 +240,14 @@ int hhg_smooth(hhg_mesh mesh, int depth, int kind, int sweeps, double omega, con
     need_vec(f_dev, "f_dev");
     need_vec(u_dev, "u_dev");
     if (sweeps < 0) throw Error{HHG_ERR_ARG, "sweeps must be >= 0"};
-    if (kind != HHG_SMOOTH_JACOBI && kind != HHG_SMOOTH_CHEBYSHEV)
-      throw Error{HHG_ERR_ARG, "hhg_smooth supports JACOBI and CHEBYSHEV"};
+    if (kind != HHG_SMOOTH_JACOBI && kind != HHG_SMOOTH_CHEBYSHEV && kind != HHG_SMOOTH_LEARNED)
+      throw Error{HHG_ERR_ARG, "unknown smoother"};
     init_launch_configs(dtype);
-    smooth(m, depth, dtype, kind, sweeps, omega, f_dev, u_dev, false, (cudaStream_t)stream);
+    if (kind == HHG_SMOOTH_LEARNED) {
+      if (depth + 1 >= m.ndepth) throw Error{HHG_ERR_ARG, "the coarsest depth is not smoothed"};
+      learned_prepare(m, dtype, (cudaStream_t)stream);
+    }
+    smooth(m, depth, dtype, kind, sweeps, omega, f_dev, u_dev, false, (cudaStream_t)stream, false);
   });
 }
 
@@ -409,3 +419,60 @@ int hhg_device_status(hhg_mesh mesh) {
 const char* hhg_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---- learned smoother ---------------------------------------------------------
+
+int hhg_learned_train(hhg_mesh mesh, const hhg_learn_params* p, hhg_learn_stats* stats, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_coef(m);
+    need_ptr(p, "params");
+    cudaStream_t s = (cudaStream_t)stream;
+    init_launch_configs(HHG_F32);
+    init_launch_configs(HHG_F64);
+    learned_train(m, *p, stats, s);
+  });
+}
+
+int hhg_learned_set_weights(hhg_mesh mesh, const float* w_host, int weights_bf16) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_ptr(w_host, "w_host");
+    learned_set_weights(m, w_host, weights_bf16, nullptr);
+  });
+}
+
+int hhg_learned_get_weights(hhg_mesh mesh, float* w_host) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_ptr(w_host, "w_host");
+    learned_get_weights(m, w_host, nullptr);
+  });
+}
+
+int hhg_learned_forward(hhg_mesh mesh, int depth, const void* r_dev, void* c_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_coef(m);
+    need_vec(r_dev, "r_dev");
+    need_vec(c_dev, "c_dev");
+    init_launch_configs(HHG_F64);
+    learned_forward(m, depth, static_cast<const float*>(r_dev), static_cast<float*>(c_dev), (cudaStream_t)stream);
+  });
+}
+
+int hhg_learned_loss_grad(hhg_mesh mesh, int depth, const void* r_dev, const void* e_dev, double* loss,
+                          double* grad_host, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_coef(m);
+    need_vec(r_dev, "r_dev");
+    need_vec(e_dev, "e_dev");
+    init_launch_configs(HHG_F32);
+    init_launch_configs(HHG_F64);
+    learned_loss_grad(m, depth, static_cast<const float*>(r_dev), static_cast<const float*>(e_dev), loss, grad_host,
+                      (cudaStream_t)stream);
+  });
+}

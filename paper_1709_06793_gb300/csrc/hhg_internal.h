@@ -193,6 +193,9 @@ struct Mesh {
 };
 
 void drop_graphs(Mesh& m);
+// learned smoother (learned.cu)
+void learned_invalidate(Mesh& m);  // coefficient changed: recompute the input features
+void learned_step(Mesh& m, int d, int dtype, const void* f, const void* src, void* dst, bool nc_only, cudaStream_t s);
 
 // ---- error handling --------------------------------------------------------
 void set_error(const std::string& msg);

@@ -69,6 +69,7 @@ __global__ void inject_kernel(DepthDev C, DepthDev F, const V* __restrict__ fine
 
 void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
   drop_graphs(m);
+  learned_invalidate(m);
   for (int d = 0; d < m.ndepth; ++d) {
     Depth& D = m.depth[d];
     const size_t n = std::max<long long>(D.n_stored, 1);
@@ -242,7 +243,7 @@ void prolongate_add(Mesh& m, int depth, int dtype, const void* ec, void* uf, cud
 constexpr int kRedBlocks = 592;  // fixed (4 x 148): the summation order never changes
 constexpr int kRedThreads = 256;
 
-enum RedPost { RED_STORE = 0, RED_ALPHA = 1, RED_BETA = 2 };
+enum RedPost { RED_STORE = 0, RED_ALPHA = 1, RED_BETA = 2, RED_FBETA = 3 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -275,6 +276,9 @@ __device__ void block_finish(double v, double* partials, unsigned* counter, doub
       S[2] = S[0] / tot;
     } else if (post == RED_BETA) {  // beta = rz_new / rz; rz = rz_new
       S[5] = tot / S[0];
+      S[0] = tot;
+    } else if (post == RED_FBETA) {  // flexible CG: beta = (rz_new - alpha z.q) / rz, z.q in S[8]
+      S[5] = (tot - S[2] * S[8]) / S[0];
       S[0] = tot;
     }
     *counter = 0;
@@ -581,10 +585,25 @@ static void copy_vec(Mesh& m, int depth, int dtype, const void* src, void* dst, 
 double lambda_max(Mesh& m, int depth, int its, cudaStream_t s);
 
 // Smoothing in place on u (workspace slots 4, 5 and 6 of the depth).
+// post = false: sweeps run Jacobi, learned, Jacobi, ...; post = true: learned,
+// Jacobi, ... (HHG_SMOOTH_LEARNED only)
 void smooth(Mesh& m, int depth, int dtype, int kind, int sweeps, double omega, const void* f, void* u, bool nc_only,
-            cudaStream_t s) {
+            cudaStream_t s, bool post) {
   const int pr = prec_of(dtype);
   void* w = workspace(m, depth, pr, 4);
+  if (kind == HHG_SMOOTH_LEARNED) {
+    void* a = u;
+    void* b = w;
+    for (int it = 0; it < sweeps; ++it) {
+      if ((it % 2 == 0) == post)
+        learned_step(m, depth, dtype, f, a, b, nc_only, s);
+      else
+        op(m, depth, dtype, OP_JACOBI, a, f, b, nullptr, nullptr, omega, 0, 0, nc_only, s);
+      std::swap(a, b);
+    }
+    if (a != u) copy_vec(m, depth, dtype, a, u, nc_only, s);
+    return;
+  }
   if (kind == HHG_SMOOTH_JACOBI) {
     void* a = u;
     void* b = w;
@@ -724,7 +743,7 @@ void vcycle(Mesh& m, int dtype, int nu1, int nu2, int smoother, double omega, co
     const Depth& D = m.depth[d];
     if (!D.n_slots_nc) continue;
     void* r = workspace(m, d, pr, 2);
-    smooth(m, d, dtype, smoother, nu1, omega, F[d], U[d], true, s);
+    smooth(m, d, dtype, smoother, nu1, omega, F[d], U[d], true, s, false);
     residual(m, d, dtype, F[d], U[d], r, true, s);
     restrict_residual(m, d, dtype, r, F[d + 1], s);
     HHG_CUDA(cudaMemsetAsync(U[d + 1], 0, m.depth[d + 1].n_stored * elem_size(dtype), s));
@@ -734,7 +753,7 @@ void vcycle(Mesh& m, int dtype, int nu1, int nu2, int smoother, double omega, co
     const Depth& D = m.depth[d];
     if (!D.n_slots_nc) continue;
     prolongate_add(m, d, dtype, U[d + 1], U[d], s);
-    smooth(m, d, dtype, smoother, nu2, omega, F[d], U[d], true, s);
+    smooth(m, d, dtype, smoother, nu2, omega, F[d], U[d], true, s, true);
   }
 }
 

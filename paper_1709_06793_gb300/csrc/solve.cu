@@ -19,8 +19,10 @@ void ensure_coarse(Mesh& m, int dtype, cudaStream_t s);
 const int* coarse_slot_map(Mesh& m, int depth);
 void init_launch_configs(int dtype);
 void learned_prepare(Mesh& m, int dtype, cudaStream_t s);
+bool learned_accepted(Mesh& m);
+void random_vector(Mesh& m, int d, float* x, unsigned long long key, cudaStream_t s);
 
-enum { RED_STORE = 0, RED_ALPHA = 1, RED_BETA = 2 };
+enum { RED_STORE = 0, RED_ALPHA = 1, RED_BETA = 2, RED_FBETA = 3 };
 
 static int prec_of(int dtype) { return elem_size(dtype) == 8 ? 0 : 1; }
 
@@ -95,7 +97,13 @@ static void pcg_body(Mesh& m, int dtype, const hhg_solve_params& p, void* x, voi
   const int g = grid_for(n, 256, 8 * m.num_sms);
   HHG_CUDA(cudaMemsetAsync(z, 0, n * elem_size(dtype), s));
   vcycle(m, dtype, p.nu1, p.nu2, p.smoother, p.omega, r, z, s);
-  dot(m, 0, dtype, r, z, 4, RED_BETA, false, s);  // beta = rz_new / rz; rz = rz_new
+  if (p.smoother == HHG_SMOOTH_LEARNED) {
+    // nonlinear preconditioner: flexible CG, r_new - r_old = -alpha q
+    dot(m, 0, dtype, z, q, 8, RED_STORE, false, s);
+    dot(m, 0, dtype, r, z, 4, RED_FBETA, false, s);
+  } else {
+    dot(m, 0, dtype, r, z, 4, RED_BETA, false, s);  // beta = rz_new / rz; rz = rz_new
+  }
   if (elem_size(dtype) == 8)
     xpay_kernel2<double><<<g, 256, 0, s>>>((double*)pp, (const double*)z, n, m.d_scalars);
   else
@@ -134,6 +142,10 @@ static PcgResult pcg(Mesh& m, int dtype, const hhg_solve_params& p, void* x, voi
   // first iteration: beta = 0 (rz = +inf), p = 0
   HHG_CUDA(cudaMemsetAsync(pp, 0, n * elem_size(dtype), s));
   set_scalar_kernel<<<1, 1, 0, s>>>(m.d_scalars, 0, INFINITY);
+  if (p.smoother == HHG_SMOOTH_LEARNED) {  // flexible beta of the first iteration: (rz - 0 * z.0) / inf = 0
+    HHG_CUDA(cudaMemsetAsync(q, 0, n * elem_size(dtype), s));
+    set_scalar_kernel<<<1, 1, 0, s>>>(m.d_scalars, 2, 0.0);
+  }
   cudaGraphExec_t exec = nullptr;
   if (p.use_graph) {
     for (auto& g : m.graphs)
@@ -162,6 +174,31 @@ static PcgResult pcg(Mesh& m, int dtype, const hhg_solve_params& p, void* x, voi
   return {std::min(it, maxit), rr};
 }
 
+// Residual reduction per iteration of `its` FP32 PCG iterations on A x = A e
+// (e a consistent random vector) from x = 0.
+double pcg_rate(Mesh& m, int dtype, int smoother, int nu1, int nu2, double omega, int its, unsigned long long seed,
+                cudaStream_t s) {
+  HHG_REQUIRE(elem_size(dtype) == 4, "pcg_rate runs on FP32 vectors");
+  prepare(m, dtype, smoother, s);
+  float* x = static_cast<float*>(workspace(m, 0, 1, 8));
+  float* r = static_cast<float*>(workspace(m, 0, 1, 0));
+  float* e = static_cast<float*>(workspace(m, 0, 1, 9));
+  random_vector(m, 0, e, seed, s);
+  apply_scaled(m, 0, dtype, e, r, s);
+  HHG_CUDA(cudaMemsetAsync(x, 0, m.depth[0].n_stored * 4, s));
+  dot(m, 0, dtype, r, r, 3, RED_STORE, false, s);
+  const double rr0 = read_scalar(m, 3, s);
+  hhg_solve_params p{};
+  p.smoother = smoother;
+  p.nu1 = nu1;
+  p.nu2 = nu2;
+  p.omega = omega;
+  p.use_graph = 0;
+  const PcgResult res = pcg(m, dtype, p, x, r, 0.0, its, s);
+  if (!(res.rr >= 0) || rr0 <= 0 || res.its <= 0) return INFINITY;
+  return std::pow(res.rr / rr0, 0.5 / res.its);
+}
+
 int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s) {
   hhg_solve_params p = p_in;
   if (p.omega <= 0) p.omega = 2.0 / 3.0;
@@ -173,6 +210,10 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
   const auto t0 = std::chrono::steady_clock::now();
   const long long n = m.depth[0].n_stored;
   const int g = grid_for(n, 256, 8 * m.num_sms);
+  HHG_REQUIRE(p.smoother != HHG_SMOOTH_LEARNED || p.mode != HHG_SOLVE_FP64,
+              "the learned smoother runs in the FP32 inner solve (modes MIXED, MIXED_KBF16)");
+  // the plain V-cycle replaces a learned smoother that is missing or was not accepted
+  if (p.smoother == HHG_SMOOTH_LEARNED && !learned_accepted(m)) p.smoother = HHG_SMOOTH_JACOBI;
   const int outer_dtype = p.mode == HHG_SOLVE_MIXED_KBF16 ? kF64KBF16 : HHG_F64;
   int inner_dtype = HHG_F64;
   if (p.mode == HHG_SOLVE_MIXED) inner_dtype = HHG_F32;
@@ -216,6 +257,13 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
       const double target = p.inner_rtol * p.inner_rtol * rr;
       PcgResult res = pcg(m, inner_dtype, p, d32, r32, target, p.maxit - total, s);
       total += res.its;
+      if (p.smoother == HHG_SMOOTH_LEARNED && !(res.rr <= rr)) {
+        // divergence guard: a learned inner solve that did not reduce the
+        // residual is discarded and the plain V-cycle takes over
+        p.smoother = HHG_SMOOTH_JACOBI;
+        prepare(m, inner_dtype, p.smoother, s);
+        continue;
+      }
       add_f32_kernel<<<g, 256, 0, s>>>(u, d32, n);
       HHG_CUDA(cudaGetLastError());
       residual(m, 0, outer_dtype, f, u, r64, false, s);
@@ -230,6 +278,7 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
     st->outer = outer;
     st->rel_residual = rel;
     st->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    st->smoother_used = p.smoother;
   }
   return status;
 }

@@ -37,7 +37,22 @@ class SolveParams(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("rel_residual", C.c_double),
+                ("time_ms", C.c_double), ("smoother_used", C.c_int)]
+
+
+class LearnParams(C.Structure):
+    _fields_ = [("steps", C.c_int), ("pairs", C.c_int), ("lr", C.c_double), ("omega", C.c_double),
+                ("max_depth", C.c_int), ("vcycle_pairs", C.c_int), ("init_noise", C.c_double),
+                ("seed", C.c_ulonglong), ("weights_bf16", C.c_int), ("validate_its", C.c_int), ("resume", C.c_int)]
+
+
+class LearnStats(C.Structure):
+    _fields_ = [("loss_jacobi", C.c_double), ("loss_init", C.c_double), ("loss_final", C.c_double),
+                ("rho_plain", C.c_double), ("rho_learned", C.c_double), ("accepted", C.c_int), ("steps", C.c_int),
                 ("time_ms", C.c_double)]
+
+
+N_LEARNED_WEIGHTS = 1296
 
 
 def _load():
@@ -71,6 +86,11 @@ def _load():
         "hhg_set_option": [P, C.c_char_p, D],
         "hhg_device_status": [P],
         "hhg_get_option": [P, C.c_char_p, C.POINTER(D)],
+        "hhg_learned_train": [P, C.POINTER(LearnParams), C.POINTER(LearnStats), P],
+        "hhg_learned_set_weights": [P, P, I],
+        "hhg_learned_get_weights": [P, P],
+        "hhg_learned_forward": [P, I, P, P, P],
+        "hhg_learned_loss_grad": [P, I, P, P, C.POINTER(D), P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -233,7 +253,39 @@ def hhg_solve(mesh, f, u, tol=1e-8, maxit=200, mode=HHG_SOLVE_FP64, smoother=HHG
     if code != 0 and (raise_on_fail or code != -4):
         _check(code)
     return {"iterations": st.iterations, "outer": st.outer, "rel_residual": st.rel_residual,
-            "time_ms": st.time_ms, "status": STATUS.get(code, code)}
+            "time_ms": st.time_ms, "smoother_used": st.smoother_used, "status": STATUS.get(code, code)}
+
+
+def hhg_learned_train(mesh, steps=150, pairs=4, lr=3e-3, omega=2.0 / 3.0, max_depth=0, vcycle_pairs=0,
+                      init_noise=0.0, seed=0, weights_bf16=1, validate_its=8, resume=0, stream=None):
+    p = LearnParams(steps, pairs, lr, omega, max_depth, vcycle_pairs, init_noise, seed, weights_bf16, validate_its,
+                    resume)
+    st = LearnStats()
+    _check(_lib.hhg_learned_train(mesh, C.byref(p), C.byref(st), _stream(stream)))
+    return {f: getattr(st, f) for f, _ in LearnStats._fields_}
+
+
+def hhg_learned_set_weights(mesh, w, weights_bf16=1):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.shape == (N_LEARNED_WEIGHTS,)
+    _check(_lib.hhg_learned_set_weights(mesh, w.ctypes.data, int(weights_bf16)))
+
+
+def hhg_learned_get_weights(mesh):
+    w = np.zeros(N_LEARNED_WEIGHTS, dtype=np.float32)
+    _check(_lib.hhg_learned_get_weights(mesh, w.ctypes.data))
+    return w
+
+
+def hhg_learned_forward(mesh, depth, r, c, stream=None):
+    _check(_lib.hhg_learned_forward(mesh, depth, _ptr(r), _ptr(c), _stream(stream)))
+
+
+def hhg_learned_loss_grad(mesh, depth, r, e, stream=None):
+    loss = C.c_double()
+    g = np.zeros(N_LEARNED_WEIGHTS, dtype=np.float64)
+    _check(_lib.hhg_learned_loss_grad(mesh, depth, _ptr(r), _ptr(e), C.byref(loss), g.ctypes.data, _stream(stream)))
+    return loss.value, g
 
 
 def hhg_device_status(mesh):
