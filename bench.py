@@ -154,6 +154,86 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+LEARNED_LEVEL = 7
+LEARNED_WORKLOAD = ("unit cube, 6 Kuhn macro-tets, level 7 (129 nodes/edge), k=exp(2g), g a Gaussian random field "
+                    "(correlation length 0.2, contrast 1e2); 2x16-channel 3x3x3 conv smoother, BF16 weights")
+# FP32 lanes: 152 SMs x 128 lanes x 2 flops (FMA) x 2070 MHz (maximum SM clock)
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def learned_bench(H, I, torch, stream, flush):
+    """C4: train the learned smoother on the GPU, then time GMG-CG to 1e-8
+    with and without it, and time its forward kernel."""
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, LEARNED_LEVEL, COARSEST)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_coefficient(m.h, torch.tensor(I.k_learned()(xyz), device="cuda"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = H.hhg_learned_train(m.h, steps=120, pairs=4, lr=3e-3, max_depth=1, vcycle_pairs=2, init_noise=0.02,
+                             seed=3, weights_bf16=1)
+    train_s = time.perf_counter() - t0
+    fi = torch.tensor(I.f_cube_sine(xyz), device="cuda")
+    f = torch.empty_like(fi)
+    H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
+    out = {"workload": LEARNED_WORKLOAD, "stored_nodes": n, "train_s": train_s, "train": st}
+    for name, mode, sm in (("fp64", H.HHG_SOLVE_FP64, H.HHG_SMOOTH_JACOBI),
+                           ("mixed", H.HHG_SOLVE_MIXED, H.HHG_SMOOTH_JACOBI),
+                           ("mixed_learned", H.HHG_SOLVE_MIXED, H.HHG_SMOOTH_LEARNED)):
+        u = torch.zeros(n, device="cuda", dtype=torch.float64)
+        H.hhg_solve(m.h, f, u, tol=1e-8, mode=mode, smoother=sm, raise_on_fail=False)
+        u.zero_()
+        torch.cuda.synchronize()
+        r = H.hhg_solve(m.h, f, u, tol=1e-8, mode=mode, smoother=sm, raise_on_fail=False)
+        out[name] = {"ms": r["time_ms"], "iterations": r["iterations"], "rel_residual": r["rel_residual"],
+                     "smoother_used": r["smoother_used"], "status": r["status"]}
+    out["speedup_learned_vs_fp64"] = out["fp64"]["ms"] / out["mixed_learned"]["ms"]
+    out["speedup_learned_vs_mixed"] = out["mixed"]["ms"] / out["mixed_learned"]["ms"]
+    # forward kernel (one learned correction at depth 0) and one Jacobi sweep
+    rr = torch.randn(n, device="cuda", dtype=torch.float32)
+    cc = torch.empty_like(rr)
+    uu = torch.zeros_like(rr)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    H.hhg_set_option(m.h, "learned_tc_all", 1)
+    tc_ms = timed(lambda: H.hhg_learned_forward(m.h, 0, rr, cc, stream))
+    H.hhg_set_option(m.h, "learned_tc_all", 0)
+    fwd_ms = timed(lambda: H.hhg_learned_forward(m.h, 0, rr, cc, stream))
+    jac_ms = timed(lambda: H.hhg_smooth(m.h, 0, H.HHG_SMOOTH_JACOBI, 1, 2.0 / 3.0, rr, uu, H.HHG_F32, stream))
+    flops = 2 * 1296 * n  # 864 + 432 multiply-adds per stored node
+    peaks, src = _peaks()
+    ach_tc = flops / (tc_ms * 1e-3) / 1e12
+    ach = flops / (fwd_ms * 1e-3) / 1e12
+    out["forward_tensor_core"] = {
+        "ms": tc_ms, "ratio_to_jacobi": tc_ms / jac_ms,
+        "roofline": {"bound": "tensor", "achieved": ach_tc, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach_tc / peaks["bf16_tflops"], "peak_source": f"{src} bf16_tflops (burst)",
+                     "algorithmic_flops_per_launch": flops}}
+    out["forward_fp32_activations"] = {
+        "ms": fwd_ms, "ratio_to_jacobi": fwd_ms / jac_ms,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP32_ALU_TFLOPS,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "algorithmic_flops_per_launch": flops}}
+    out["jacobi_sweep_ms"] = jac_ms
+    m.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,6 +243,7 @@ def main():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tune-cache", action="store_true", help="reuse/append autotuner results in _build_tune.txt")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -281,6 +362,10 @@ def main():
                            "rhs M I_h f; FP64 outer residual in every mode")
         solve["speedup_mixed_vs_fp64"] = solve["fp64"]["ms"] / solve["mixed_fp32_fp64refine"]["ms"]
 
+    learned = None
+    if not args.no_learned:
+        learned = learned_bench(H, I, torch, stream, flush)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -293,7 +378,7 @@ def main():
                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
            "autotune": tune,
-           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve}
+           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve, "learned": learned}
     if rank == 0:
         print(json.dumps(out))
     m.close()

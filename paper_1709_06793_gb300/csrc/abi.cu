@@ -25,6 +25,7 @@ int solve(Mesh& m, const hhg_solve_params& p, const double* f, double* u, hhg_so
 void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_korder, double* out_ms, cudaStream_t s);
 void init_launch_configs(int dtype);
 void learned_prepare(Mesh& m, int dtype, cudaStream_t s);
+bool learned_option(Mesh& m, const std::string& key, double* value, bool set);
 void learned_train(Mesh& m, const hhg_learn_params& p, hhg_learn_stats* st, cudaStream_t s);
 void learned_set_weights(Mesh& m, const float* w_host, int bf16, cudaStream_t s);
 void learned_get_weights(Mesh& m, float* w_host, cudaStream_t s);
@@ -378,7 +379,7 @@ int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
       if (value < 1 || value > 1000) throw Error{HHG_ERR_ARG, "power_its must be in [1, 1000]"};
       m.power_its = (int)value;
       for (Depth& D : m.depth) D.lam = 0.0;
-    } else {
+    } else if (!learned_option(m, k, &value, true)) {
       throw Error{HHG_ERR_ARG, "unknown option '" + k + "'"};
     }
   });
@@ -396,7 +397,7 @@ int hhg_get_option(hhg_mesh mesh, const char* key, double* value) {
     else if (k == "cheb_lo") *value = m.cheb_lo;
     else if (k == "cheb_hi") *value = m.cheb_hi;
     else if (k == "power_its") *value = m.power_its;
-    else throw Error{HHG_ERR_ARG, "unknown option '" + k + "'"};
+    else if (!learned_option(m, k, value, false)) throw Error{HHG_ERR_ARG, "unknown option '" + k + "'"};
   });
 }
 

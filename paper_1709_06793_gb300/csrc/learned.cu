@@ -162,6 +162,177 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// ---- forward on the tensor cores (BF16 weights and activations, FP32 accumulate)
+// Same network and tiling as conv_fwd_kernel, evaluated with
+// mma.sync.m16n8k16 (bf16 x bf16 -> f32):
+//   layer 1  Z[p][c] = sum_k X[p][k] W1[k][c], k = 2 tau + a (54 used of 64):
+//            rows = 16 hidden points, A fragments are single 32-bit loads of
+//            the packed (a0, a1) pair at point p + tau, W1 lives in registers;
+//   layer 2  P[p][tau] = sum_c h[p][c] W2[tau][c]: the FP32 accumulators of
+//            layer 1 (after ReLU, rounded to BF16) are exactly the A fragment
+//            of this product; 27 taps padded to 32 columns;
+//   output   ch(x) = sum_tau P[x + tau][tau], gathered from shared memory.
+constexpr int kHP = kBH * kBH * kBH;          // 1000 hidden points
+constexpr int kMT = (kHP + 15) / 16;          // 63 row tiles
+constexpr int kPS = kTaps;                    // P row stride (odd: conflict-free gather)
+constexpr int kTcThreads = 512;
+constexpr size_t kTcSmem = (size_t)kBF * kBF * kBF * 4 + (size_t)kMT * 16 * kPS * 4;
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    conv_fwd_tc_kernel(DepthDev D, const int4* __restrict__ tiles, int n_tiles, const __nv_bfloat16* __restrict__ w,
+                       const float* __restrict__ r, const float2* __restrict__ feat, const float* src, float* dst,
+                       float* __restrict__ craw) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  unsigned* X2 = reinterpret_cast<unsigned*>(smb);
+  float* P = reinterpret_cast<float*>(smb + kBF * kBF * kBF * 4);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  auto wv = [&](int q) { return __bfloat162float(w[q]); };
+  // B fragments: layer 1 (k-step ks, channel tile nt), layer 2 (tap tile nt)
+  unsigned b1[4][2][2], b2[4][2];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * ks + 2 * t + 8 * h, c = 8 * nt + g;
+        const float lo = k < kTaps * kIn ? wv(k * kHid + c) : 0.f;
+        const float hi = k + 1 < kTaps * kIn ? wv((k + 1) * kHid + c) : 0.f;
+        b1[ks][nt][h] = pack_bf16(lo, hi);
+      }
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int tau = 8 * nt + g, c = 2 * t + 8 * h;
+      b2[nt][h] = tau < kTaps ? pack_bf16(wv(kNW1 + tau * kHid + c), wv(kNW1 + tau * kHid + c + 1)) : 0u;
+    }
+  // tap offsets in the input box of the A-fragment columns (taps >= 27 have zero weights)
+  int offA[4], offB[4];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    offA[ks] = tap_off(min(8 * ks + t, kTaps - 1), kBF);
+    offB[ks] = tap_off(min(8 * ks + 4 + t, kTaps - 1), kBF);
+  }
+  // the input box of the next tile is loaded into registers while the
+  // current one is computed (kPre points per thread)
+  constexpr int kPre = (kBF * kBF * kBF + kTcThreads - 1) / kTcThreads;
+  float pr[kPre], pf[kPre], pk[kPre];
+  auto prefetch = [&](int tile) {
+    const int4 tl = tiles[tile];
+    const TetDev td = D.tets[tl.x];
+#pragma unroll
+    for (int s2 = 0; s2 < kPre; ++s2) {
+      const int q = threadIdx.x + s2 * kTcThreads;
+      pr[s2] = 0.f;
+      pf[s2] = 0.f;
+      pk[s2] = 0.f;
+      if (q < kBF * kBF * kBF) {
+        const int bi = q % kBF, bj = (q / kBF) % kBF, bk = q / (kBF * kBF);
+        const int i = tl.y - 2 + bi, j = tl.z - 2 + bj, k = tl.w - 2 + bk;
+        if (in_set(td.N, i, j, k)) {
+          const long long idx = td.base + node_offset(td.N, i, j, k);
+          pr[s2] = r[idx];
+          const float2 f = feat[idx];
+          pf[s2] = f.x;
+          pk[s2] = f.y;
+        }
+      }
+    }
+  };
+  if (blockIdx.x < n_tiles) prefetch(blockIdx.x);
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int4 tl = tiles[tile];
+    const TetDev td = D.tets[tl.x];
+    const int N = td.N, i0 = tl.y, j0 = tl.z, k0 = tl.w;
+    __syncthreads();  // previous tile finished with X2 and P
+#pragma unroll
+    for (int s2 = 0; s2 < kPre; ++s2) {
+      const int q = threadIdx.x + s2 * kTcThreads;
+      if (q < kBF * kBF * kBF) {
+        const float a0 = pr[s2] * pf[s2];
+        X2[q] = pack_bf16(a0, a0 * pk[s2]);
+      }
+    }
+    __syncthreads();
+    if (tile + (int)gridDim.x < n_tiles) prefetch(tile + gridDim.x);
+    for (int mt = warp; mt < kMT; mt += nwarps) {
+      int xb[2];
+      bool ok[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = min(16 * mt + g + 8 * h, kHP - 1);
+        const int hi = p % kBH, hj = (p / kBH) % kBH, hk = p / (kBH * kBH);
+        xb[h] = (hi + 1) + kBF * (hj + 1) + kBF * kBF * (hk + 1);
+        ok[h] = 16 * mt + g + 8 * h < kHP && in_set(N, i0 - 1 + hi, j0 - 1 + hj, k0 - 1 + hk);
+      }
+      float z[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const unsigned a0 = X2[xb[0] + offA[ks]], a1 = X2[xb[1] + offA[ks]];
+        const unsigned a2 = X2[xb[0] + offB[ks]], a3 = X2[xb[1] + offB[ks]];
+        mma_bf16(z[0], a0, a1, a2, a3, b1[ks][0][0], b1[ks][0][1]);
+        mma_bf16(z[1], a0, a1, a2, a3, b1[ks][1][0], b1[ks][1][1]);
+      }
+      // h = max(z, 0) on points of the index set, as the A fragment of layer 2
+      const float m0 = ok[0] ? 1.f : 0.f, m1 = ok[1] ? 1.f : 0.f;
+      const unsigned h0 = pack_bf16(fmaxf(z[0][0], 0.f) * m0, fmaxf(z[0][1], 0.f) * m0);
+      const unsigned h1 = pack_bf16(fmaxf(z[0][2], 0.f) * m1, fmaxf(z[0][3], 0.f) * m1);
+      const unsigned h2 = pack_bf16(fmaxf(z[1][0], 0.f) * m0, fmaxf(z[1][1], 0.f) * m0);
+      const unsigned h3 = pack_bf16(fmaxf(z[1][2], 0.f) * m1, fmaxf(z[1][3], 0.f) * m1);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        float pp[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(pp, h0, h1, h2, h3, b2[nt][0], b2[nt][1]);
+        const int tau = 8 * nt + 2 * t;
+        const int r0 = (16 * mt + g) * kPS, r1 = (16 * mt + g + 8) * kPS;
+        if (tau < kTaps) {
+          P[r0 + tau] = pp[0];
+          P[r1 + tau] = pp[2];
+        }
+        if (tau + 1 < kTaps) {
+          P[r0 + tau + 1] = pp[1];
+          P[r1 + tau + 1] = pp[3];
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kT * kT * kT; q += blockDim.x) {
+      const int oi = q % kT, oj = (q / kT) % kT, ok = q / (kT * kT);
+      const int i = i0 + oi, j = j0 + oj, k = k0 + ok;
+      if (!in_set(N, i, j, k)) continue;
+      const int hb = (oi + 1) + kBH * (oj + 1) + kBH * kBH * (ok + 1);
+      float acc = 0.f;
+#pragma unroll
+      for (int tau = 0; tau < kTaps; ++tau) acc += P[(hb + tap_off(tau, kBH)) * kPS + tau];
+      const long long idx = td.base + node_offset(N, i, j, k);
+      if (OUT == 0) {
+        dst[idx] = acc;
+      } else if (face_mask(N, i, j, k)) {
+        craw[idx] = acc;
+      } else {
+        dst[idx] = src[idx] + acc;
+      }
+    }
+  }
+}
+
 // ---- interface / Dirichlet pass -------------------------------------------
 // mode 0: x <- mean over copies of x (Dirichlet: 0)             (training forward)
 // mode 1: x_dst <- x_src + mean over copies of y (Dirichlet: x_src)  (smoothing step)
@@ -417,6 +588,8 @@ struct Learned {
   double* grad = nullptr;         // [1296]
   int nblk = 0;
   bool have_weights = false, bf16 = true, feat_valid = false, accepted = false;
+  bool tc = true;       // BF16 forward on the tensor cores (smoothing steps)
+  bool tc_all = false;  // also for the exact forward (hhg_learned_forward, training)
   int adam_t = 0;
 };
 
@@ -449,6 +622,8 @@ void init_kernels_smem() {
   HHG_CUDA(cudaFuncSetAttribute(conv_fwd_kernel<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kFwdSmem));
   HHG_CUDA(cudaFuncSetAttribute(conv_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem));
+  HHG_CUDA(cudaFuncSetAttribute(conv_fwd_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+  HHG_CUDA(cudaFuncSetAttribute(conv_fwd_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   HHG_CUDA(cudaFuncSetAttribute(conv_bwd_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kBwdSmem));
   done = true;
@@ -526,7 +701,10 @@ void launch_fwd(Mesh& m, Learned& L, int d, const float* r, const float* src, fl
   if (nt == 0) return;
   const int g = std::min(nt, L.nblk);
   const DepthDev& DD = m.depth[d].dev;
-  if (L.bf16)
+  if (L.bf16 && (OUT == 1 ? L.tc : L.tc_all))
+    conv_fwd_tc_kernel<OUT><<<std::min(nt, std::max(m.num_sms, 1)), kTcThreads, kTcSmem, s>>>(DD, X.tiles, nt, L.w16, r,
+                                                                                              X.feat, src, dst, craw);
+  else if (L.bf16)
     conv_fwd_kernel<__nv_bfloat16, OUT><<<g, kThreads, kFwdSmem, s>>>(DD, X.tiles, nt, L.w16, r, X.feat, src, dst, craw);
   else
     conv_fwd_kernel<float, OUT><<<g, kThreads, kFwdSmem, s>>>(DD, X.tiles, nt, L.w32, r, X.feat, src, dst, craw);
@@ -642,6 +820,24 @@ void learned_get_weights(Mesh& m, float* w_host, cudaStream_t s) {
   HHG_REQUIRE(L.have_weights, "learned smoother has no weights");
   HHG_CUDA(cudaMemcpyAsync(w_host, L.w32, kNW * 4, cudaMemcpyDeviceToHost, s));
   HHG_CUDA(cudaStreamSynchronize(s));
+}
+
+// "learned_tc": BF16 smoothing steps on the tensor cores (1, default) or the
+// FP32-activation kernel (0); "learned_tc_all": the same for hhg_learned_forward
+// and the training forward (default 0).
+bool learned_option(Mesh& m, const std::string& key, double* value, bool set) {
+  if (key != "learned_tc" && key != "learned_tc_all") return false;
+  if (!m.device) throw Error{HHG_ERR_STATE, "mesh was created host-only"};
+  Learned& L = state(m);
+  bool& f = key == "learned_tc" ? L.tc : L.tc_all;
+  if (set) {
+    if (*value != 0.0 && *value != 1.0) throw Error{HHG_ERR_ARG, key + " must be 0 or 1"};
+    f = *value != 0.0;
+    drop_graphs(m);
+  } else {
+    *value = f ? 1.0 : 0.0;
+  }
+  return true;
 }
 
 bool learned_accepted(Mesh& m) { return m.learned && state(m).have_weights && state(m).accepted; }

@@ -139,6 +139,34 @@ def test_loss_and_gradient_match_oracle(H, bf16, d):
     c.close()
 
 
+@pytest.mark.parametrize("d", [0, 1])
+def test_tensor_core_forward_matches_oracle(H, d):
+    """BF16 forward on the tensor cores (mma.sync, BF16 inputs and hidden
+    activations, FP32 accumulation).  Rounding the two input channels and the
+    16 hidden channels to BF16 (2^-9 relative each) before FP32 sums of 54 and
+    432 products bounds the error by a few 2^-9 of the largest value: 1e-2."""
+    c = Case(H)
+    rng = np.random.default_rng(80 + d)
+    w = rng.normal(0, 0.3, LO.N_W).astype(np.float32)
+    H.hhg_learned_set_weights(c.m.h, w, weights_bf16=1)
+    H.hhg_set_option(c.m.h, "learned_tc_all", 1)
+    assert H.hhg_get_option(c.m.h, "learned_tc_all") == 1
+    r, e = c.pair(d, 90 + d)
+    lm, mp, n = c.depth(d)
+    diag, k = c.diag_k(d)
+    cg = torch.zeros(n, device="cuda", dtype=torch.float32)
+    H.hhg_learned_forward(c.m.h, d, c.dev(d, r), cg)
+    H.hhg_set_option(c.m.h, "learned_tc_all", 0)
+    cf = torch.zeros(n, device="cuda", dtype=torch.float32)
+    H.hhg_learned_forward(c.m.h, d, c.dev(d, r), cf)
+    cg = cg.cpu().numpy().astype(np.float64)
+    ref = LO.forward(lm, bf16_round(w), *LO.features(lm, r, diag, k))[0][mp]
+    assert rel_err(cg, ref) <= 1e-2
+    assert rel_err(cg, cf.cpu().numpy().astype(np.float64)) <= 1e-2
+    assert rel_err(cg, ref) > 0  # the two paths are distinct kernels
+    c.close()
+
+
 def test_jacobi_network_is_a_jacobi_sweep(H):
     """Weights equal to damped Jacobi (omega = 1/2, exact in BF16): the
     learned correction is one Jacobi sweep from zero."""
@@ -182,6 +210,35 @@ def test_learned_smoothing_matches_oracle_composition(H):
     u = u + LO.forward(lm, w, *LO.features(lm, res, diag, k))[0]
     u[I_] = c.Ho.jacobi(l, f[I_], u[I_], 1)
     assert rel_err(ud.cpu().numpy().astype(np.float64), u[mp]) <= 1e-5
+    c.close()
+
+
+def test_tensor_core_smoothing_matches_oracle_composition(H):
+    """hhg_smooth(LEARNED, 2 sweeps) with BF16 weights on the tensor cores =
+    Jacobi then learned step (oracle, BF16-rounded weights), within the BF16
+    activation bound of the correction (1e-2 of the correction's size)."""
+    c = Case(H)
+    rng = np.random.default_rng(61)
+    w = LO.jacobi_weights(2.0 / 3.0, noise=rng.normal(0, 0.05, LO.N_W)).astype(np.float32)
+    H.hhg_learned_set_weights(c.m.h, w, weights_bf16=1)
+    lm, mp, n = c.depth(0)
+    l = c.level
+    A = c.Ho.A[l]
+    diag, k = c.diag_k(0)
+    x = lm.coords
+    f = np.where(lm.dirichlet, 0.0, np.sin(3 * x[:, 0] + x[:, 1]) * np.cos(2 * x[:, 2])).astype(np.float32)
+    u0 = np.where(lm.dirichlet, 0.0, np.cos(2 * x[:, 0] - x[:, 1] + 3 * x[:, 2])).astype(np.float32)
+    f, u0 = f.astype(np.float64), u0.astype(np.float64)
+    ud = c.dev(0, u0)
+    H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_LEARNED, 2, 2.0 / 3.0, c.dev(0, f), ud, H.HHG_F32)
+    I_ = lm.unknowns
+    u = u0.copy()
+    u[I_] = c.Ho.jacobi(l, f[I_], u[I_], 1)
+    res = np.zeros(lm.n)
+    res[I_] = f[I_] - A @ u[I_]
+    corr = LO.forward(lm, bf16_round(w), *LO.features(lm, res, diag, k))[0]
+    got = ud.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - (u + corr)[mp])) <= 1e-2 * np.max(np.abs(corr))
     c.close()
 
 
