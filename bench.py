@@ -263,6 +263,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--only-learned", action="store_true",
+                    help="run only the learned-smoother section (C4) and print its JSON")
     ap.add_argument("--tune-cache", action="store_true", help="reuse/append autotuner results in _build_tune.txt")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -277,6 +279,13 @@ def main():
     from paper_1709_06793_gb300 import build, inputs as I
     build.build()
     from paper_1709_06793_gb300 import hhg as H
+
+    if args.only_learned:
+        flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+        out = learned_bench(H, I, torch, torch.cuda.current_stream(), flush)
+        if rank == 0:
+            print(json.dumps({"learned": out}))
+        return
 
     V, T = I.kuhn_cube()
     m = H.Mesh(V, T, args.level, COARSEST)
