@@ -206,6 +206,14 @@ int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int
 int hhg_autotune(hhg_mesh mesh, int dtype, const char* cache_path, int* kseg, int* korder, double* best_ms,
                  void* stream);
 
+/* y = A_I(k) u, the "scale Vol+Face" operator of Sec. 5 (eq. "modst" with
+ * I = W_V u W_E): rows of nodes on macro vertices and edges are the
+ * nodal-integration rows of eq. "standardfe", all other rows the scaled rows
+ * of hhg_apply_scaled.  Reproduces affine solutions for affine k (Lemma
+ * "repro"); not symmetric (the asymmetry is O(h^2)).  Arguments, layout and
+ * errors as hhg_apply_scaled; u_dev and y_dev must not overlap. */
+int hhg_apply_volface(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
+
 /* r = f - A_s(k) u at `depth` (the residual of the paper's benchmark, Sec. 7.4). */
 int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev,
                  int dtype, void* stream);

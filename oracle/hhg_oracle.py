@@ -15,6 +15,8 @@ It computes, from the paper's definitions and nothing else,
   Lemma "equal" / eq. "equal": K_t o A_t with off-diagonal (k_i+k_j)/2 and the
   diagonal fixed by the zero row sum of eq. "zerosum";
 * the nodal-integration operator of eq. "standardfe": mean vertex k times A_t;
+* the "scale Vol+Face" operator of eq. "modst" (nodal rows on macro vertices
+  and edges, scaled rows elsewhere);
 * the consistent P1 mass matrix (right-hand side f_h = M I_h f, Sec. 7.2);
 * global assembly over unique nodes (nodes on macro faces/edges/vertices are
   shared by all macro tetrahedra that contain them, Sec. 2.1), homogeneous
@@ -341,6 +343,39 @@ class LevelMesh:
         A = self.assemble(k, kind)
         I = self.unknowns
         return A[I][:, I].tocsr()
+
+
+# ----------------------------------------------------------------------------
+# "Scale Vol+Face" (Sec. 5, eq. "modst" with I = W_V u W_E): rows of nodes on
+# macro vertices and edges come from the nodal-integration form of
+# eq. "standardfe", all other rows (macro faces, volumes) from stencil scaling.
+# ----------------------------------------------------------------------------
+
+
+def primitive_dim(lm):
+    """Dimension of the macro primitive holding each unique node: 0 vertex,
+    1 edge, 2 face, 3 volume (number of non-zero barycentric weights - 1)."""
+    return np.count_nonzero(lm.ident[:, 1::2], axis=1) - 1
+
+
+def volface_rows(lm):
+    """Rows taken from the nodal-integration form: nodes on macro vertices and
+    edges (the index set I = W_V u W_E of eq. "modst")."""
+    return primitive_dim(lm) <= 1
+
+
+def volface_matrix(lm, k):
+    """Full n x n matrix of a_{h;I} (Dirichlet rows and columns kept)."""
+    sel = volface_rows(lm).astype(np.float64)
+    An = lm.assemble(k, "nodal")
+    As = lm.assemble(k, "scaled")
+    return (sp.diags(sel) @ An + sp.diags(1.0 - sel) @ As).tocsr()
+
+
+def volface_apply(lm, u, k):
+    """y = a_{h;I}(u, .) on the unknowns (Dirichlet entries of u taken as 0,
+    those of y set to 0), from the two element loops."""
+    return np.where(volface_rows(lm), lm.apply(u, k, "nodal"), lm.apply(u, k, "scaled"))
 
 
 # ----------------------------------------------------------------------------

@@ -195,6 +195,21 @@ int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, in
   });
 }
 
+int hhg_apply_volface(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    need_dtype(dtype);
+    need_coef(m);
+    need_vec(u_dev, "u_dev");
+    need_vec(y_dev, "y_dev");
+    if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
+    init_launch_configs(dtype);
+    OpArgs a{u_dev, nullptr, y_dev, nullptr, nullptr, 0, 0, 0, 0};
+    launch_volface_op(m, depth, dtype, OP_APPLY, a, (cudaStream_t)stream);
+  });
+}
+
 int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
   return guarded([&] {
     Mesh& m = need(mesh);

@@ -670,9 +670,12 @@ constexpr NodalTable make_nodal_table() {
 
 __constant__ NodalTable kNodal = make_nodal_table();
 
-template <class T, class KT>
+// Partial nodal-integration row of one copy; with DIAG the copy's part of the
+// diagonal (-sum of the off-diagonal entries) is subtracted into *dg.
+template <class T, class KT, bool DIAG = false>
 __device__ __forceinline__ T nodal_partial(const TetDev& td, const T* __restrict__ elem, int i, int j, int k,
-                                           const T* __restrict__ u, const KT* __restrict__ kk, bool check) {
+                                           const T* __restrict__ u, const KT* __restrict__ kk, bool check,
+                                           T* dg = nullptr) {
   const int N = td.N;
   const long long x = td.base + node_offset(N, i, j, k);
   const T ux = u[x], kx = (T)ldk(kk, x);
@@ -689,7 +692,7 @@ __device__ __forceinline__ T nodal_partial(const TetDev& td, const T* __restrict
       idx[q] = td.base + node_offset(N, a, b, c);
     }
     if (!ok) continue;
-    T ksum = 0, inner = 0;
+    T ksum = 0, inner = 0, asum = 0;
     const T* A = elem + E.sigma * 16 + E.v * 4;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -698,9 +701,11 @@ __device__ __forceinline__ T nodal_partial(const TetDev& td, const T* __restrict
       } else {
         ksum += (T)ldk(kk, idx[q]);
         inner = fma(A[q], u[idx[q]] - ux, inner);
+        if (DIAG) asum += A[q];
       }
     }
     y = fma(ksum, inner, y);
+    if (DIAG) *dg = fma(-ksum, asum, *dg);
   }
   return y;
 }
@@ -959,6 +964,78 @@ static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk,
     nodal_boundary_kernel<T, KT><<<(D.n_bnodes + 127) / 128, 128, 0, s>>>(
         D, static_cast<const T*>(u), static_cast<const KT*>(kk), static_cast<T*>(y));
     HHG_CUDA(cudaGetLastError());
+  }
+}
+
+// ---------------------------------------------------------------------------
+// "Scale Vol+Face" (Sec. 5, eq. "modst" with I = W_V u W_E): after the scaled
+// launch, the rows of nodes on macro vertices and edges (face mask with two or
+// more bits in every containing tet) are replaced by their nodal-integration
+// rows, summed over the copies and written to every copy, with the same
+// residual / Jacobi / diagonal epilogue as the scaled kernel.
+// ---------------------------------------------------------------------------
+template <class T, class KT, int MODE>
+__global__ void volface_fixup_kernel(DepthDev D, OpPtrs p, int n_b) {
+  const T* elem;
+  if constexpr (sizeof(T) == 8)
+    elem = reinterpret_cast<const T*>(D.elem64);
+  else
+    elem = reinterpret_cast<const T*>(D.elem32);
+  const T* u = static_cast<const T*>(p.u);
+  const KT* kk = static_cast<const KT*>(p.k);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += gridDim.x * blockDim.x) {
+    const int lo = D.bstart[b], hi = D.bstart[b + 1];
+    if (D.bdir[b] || __popc((unsigned)D.bcopies[lo].mask) < 2) continue;
+    T y = 0, dg = 0;
+    for (int q = lo; q < hi; ++q) {
+      const BCopy cp = D.bcopies[q];
+      y += nodal_partial<T, KT, true>(D.tets[cp.slot], elem + cp.slot * 96, cp.i, cp.j, cp.k, u, kk, true, &dg);
+    }
+    const long long i0 = D.bcopies[lo].idx;
+    T val = y;
+    if (MODE == OP_RESID) {
+      val = static_cast<const T*>(p.f)[i0] - y;
+    } else if (MODE == OP_JACOBI) {
+      val = u[i0] + (T)p.omega * (static_cast<const T*>(p.f)[i0] - y) / dg;
+    } else if (MODE == OP_DIAG) {
+      val = dg;
+    }
+    for (int q = lo; q < hi; ++q) static_cast<T*>(p.out)[D.bcopies[q].idx] = val;
+  }
+}
+
+template <class T, class KT, int MODE>
+static void volface_typed(const Mesh& m, int depth, const OpArgs& a, const void* kptr, cudaStream_t s) {
+  const DepthDev& D = m.depth[depth].dev;
+  const int n_b = a.nc_only ? D.n_bnodes_nc : D.n_bnodes;
+  if (n_b == 0) return;
+  OpPtrs p{a.u, kptr, a.f, a.out, nullptr, nullptr, a.omega, 0, 0};
+  volface_fixup_kernel<T, KT, MODE><<<std::min((n_b + 127) / 128, 8 * m.num_sms), 128, 0, s>>>(D, p, n_b);
+  HHG_CUDA(cudaGetLastError());
+}
+
+template <int MODE>
+static void volface_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, cudaStream_t s) {
+  const Depth& Dh = m.depth[depth];
+  if (dtype == HHG_F64)
+    volface_typed<double, double, MODE>(m, depth, a, Dh.k64, s);
+  else if (dtype == kF64KBF16)
+    volface_typed<double, double, MODE>(m, depth, a, Dh.k16d, s);
+  else if (dtype == HHG_F32)
+    volface_typed<float, float, MODE>(m, depth, a, Dh.k32, s);
+  else
+    volface_typed<float, __nv_bfloat16, MODE>(m, depth, a, Dh.k16, s);
+}
+
+void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
+  HHG_REQUIRE(mode != OP_CHEB, "the Vol+Face operator has no Chebyshev mode");
+  launch_scaled_op(m, depth, dtype, mode, a, s);
+  switch (mode) {
+    case OP_APPLY: volface_mode<OP_APPLY>(m, depth, dtype, a, s); break;
+    case OP_RESID: volface_mode<OP_RESID>(m, depth, dtype, a, s); break;
+    case OP_JACOBI: volface_mode<OP_JACOBI>(m, depth, dtype, a, s); break;
+    case OP_DIAG: volface_mode<OP_DIAG>(m, depth, dtype, a, s); break;
+    default: break;
   }
 }
 

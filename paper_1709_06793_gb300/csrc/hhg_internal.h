@@ -245,6 +245,8 @@ struct OpArgs {
 
 void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
+// scaled launch followed by the nodal-integration rows of macro vertices and edges (eq. "modst")
+void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 
 }  // namespace hhg

@@ -72,6 +72,7 @@ def _load():
         "hhg_set_coefficient": [P, P, P],
         "hhg_apply_scaled": [P, I, P, P, I, P],
         "hhg_apply_nodal": [P, I, P, P, I, P],
+        "hhg_apply_volface": [P, I, P, P, I, P],
         "hhg_residual": [P, I, P, P, P, I, P],
         "hhg_apply_mass": [P, I, P, P, I, P],
         "hhg_autotune": [P, I, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D), P],
@@ -196,6 +197,10 @@ def hhg_apply_scaled(mesh, depth, u, y, dtype, stream=None):
 
 def hhg_apply_nodal(mesh, depth, u, y, dtype, stream=None):
     _check(_lib.hhg_apply_nodal(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_apply_volface(mesh, depth, u, y, dtype, stream=None):
+    _check(_lib.hhg_apply_volface(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
 
 
 def hhg_apply_mass(mesh, depth, u, y, dtype, stream=None):

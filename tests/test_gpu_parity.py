@@ -116,6 +116,31 @@ def test_apply_parity(H, case, kind, dtype):
     assert np.all(got[case.dir] == 0)
 
 
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_volface_apply_parity(H, case, dtype):
+    """"Scale Vol+Face" (eq. "modst", I = W_V u W_E) against the oracle's
+    row split of its nodal and scaled element loops."""
+    u = case.rand_or
+    tol = 1e-12 if dtype == H.HHG_F64 else 1e-6
+    uin = u if dtype == H.HHG_F64 else _f32(u)
+    ud = case.dev(uin, dtype)
+    y = torch.empty_like(ud)
+    H.hhg_apply_volface(case.m.h, 0, ud, y, dtype)
+    torch.cuda.synchronize()
+    got = case.back(y)
+    want = O.volface_apply(case.lm, uin, case.kprec(dtype))
+    assert _rel(got, want) <= tol, _rel(got, want)
+    assert np.all(got[case.dir] == 0)
+    # it differs from plain scaling exactly on macro-vertex/edge rows
+    ys = torch.empty_like(ud)
+    H.hhg_apply_scaled(case.m.h, 0, ud, ys, dtype)
+    diff = np.abs(got - case.back(ys)) > 0
+    ve = O.volface_rows(case.lm) & ~case.dir
+    assert not np.any(diff & ~ve)
+    if ve.any() and dtype == H.HHG_F64:
+        assert np.any(diff & ve)
+
+
 def test_scaled_and_nodal_differ_for_nonaffine_k(H, case):
     ud = case.dev(case.rand_or, H.HHG_F64)
     ys, yn = torch.empty_like(ud), torch.empty_like(ud)
