@@ -78,8 +78,15 @@ typedef enum {
 typedef enum {
     HHG_SOLVE_FP64 = 0,        /* plain FP64 GMG-preconditioned CG */
     HHG_SOLVE_MIXED = 1,       /* FP64 iterative refinement around FP32 GMG-CG */
-    HHG_SOLVE_MIXED_KBF16 = 2  /* as MIXED, bfloat16 k in the FP32 inner solve */
+    HHG_SOLVE_MIXED_KBF16 = 2, /* as MIXED, bfloat16 k in the FP32 inner solve */
+    HHG_SOLVE_MG = 3           /* FP64 multigrid as the solver: u <- V(nu1,nu2)(f, u) (Sec. 7.2) */
 } hhg_solve_mode;
+
+typedef enum {
+    HHG_OP_SCALED = 0,         /* stencil scaling on every row (eq. "discrete") */
+    HHG_OP_VOLFACE = 1,        /* "scale Vol+Face": nodal rows on macro vertices/edges (eq. "modst") */
+    HHG_OP_NODAL = 2           /* nodal integration on every row (eq. "standardfe") */
+} hhg_operator;
 
 typedef struct {
     double tol;          /* stop when ||f - A u||_2 / ||f||_2 <= tol (unique unknowns) */
@@ -91,6 +98,8 @@ typedef struct {
     double inner_rtol;   /* MIXED: relative residual reduction of each inner solve (default 1e-4) */
     int max_outer;       /* MIXED: max refinement steps (default 20) */
     int use_graph;       /* capture each CG iteration in a CUDA graph (1) or launch eagerly (0) */
+    int op;              /* hhg_operator; HHG_OP_VOLFACE and HHG_OP_NODAL need mode HHG_SOLVE_MG
+                            and Jacobi smoothing (coarsest level: dense LU of that operator) */
 } hhg_solve_params;
 
 typedef struct {
@@ -100,6 +109,8 @@ typedef struct {
     double time_ms;      /* wall time of the call */
     int smoother_used;   /* smoother of the last inner solve (HHG_SMOOTH_JACOBI if a
                             requested learned smoother was not accepted or diverged) */
+    double rho;          /* HHG_SOLVE_MG: convergence rate (r^(i*) / r^(5))^(1/(i*-5)) of the
+                            residual 2-norms, i* = cycles taken (Sec. 7); 0 otherwise */
 } hhg_solve_stats;
 
 /* Training of the learned smoother (hhg_learned_train); fields <= 0 take the

@@ -339,8 +339,9 @@ class LevelMesh:
         return y
 
     def system(self, k, kind="scaled"):
-        """A_II: the operator restricted to unknown (non-Dirichlet) nodes."""
-        A = self.assemble(k, kind)
+        """A_II: the operator restricted to unknown (non-Dirichlet) nodes
+        (kind "scaled", "nodal" or "volface")."""
+        A = volface_matrix(self, k) if kind == "volface" else self.assemble(k, kind)
         I = self.unknowns
         return A[I][:, I].tocsr()
 
@@ -486,7 +487,11 @@ class Hierarchy:
             Pf = prolongation(self.mesh[l - 1], self.mesh[l])
             self.P[l] = Pf[self.mesh[l].unknowns][:, self.mesh[l - 1].unknowns].tocsr()
         Ac = self.A[coarsest].toarray()
-        self.chol = np.linalg.cholesky(Ac)
+        self.kind = kind
+        if kind == "volface":  # not symmetric: LU on the coarsest level
+            self.lu = sla.lu_factor(Ac)
+        else:
+            self.chol = np.linalg.cholesky(Ac)
         self.smoother, self.omega = smoother, omega
         self.cheb_degree, self.cheb_lo, self.cheb_hi = cheb_degree, cheb_lo, cheb_hi
         self.lam = {l: self.lambda_max(l, power_its) for l in self.levels}
@@ -517,6 +522,8 @@ class Hierarchy:
         return lam
 
     def coarse_solve(self, f):
+        if self.kind == "volface":
+            return sla.lu_solve(self.lu, f)
         y = sla.solve_triangular(self.chol, f, lower=True)
         return sla.solve_triangular(self.chol.T, y, lower=False)
 
@@ -591,6 +598,19 @@ class Hierarchy:
             rz = rz_new
         return x, it, hist
 
+    def mg_solve(self, f, its, nu1=3, nu2=3, x0=None):
+        """Multigrid as the solver (Sec. 7.2: V(3,3) cycles, i* = 10): x <-
+        V-cycle(f, x) from x0 = 0; returns x and the residual 2-norms r^(i),
+        i = 0..its."""
+        l = self.finest
+        A = self.A[l]
+        x = np.zeros_like(f) if x0 is None else x0.copy()
+        hist = [float(np.linalg.norm(f - A @ x))]
+        for _ in range(its):
+            x = self.vcycle(l, f, x, nu1, nu2)
+            hist.append(float(np.linalg.norm(f - A @ x)))
+        return x, hist
+
     def direct_solve(self, f):
         return spla.spsolve(self.A[self.finest].tocsc(), f)
 
@@ -598,6 +618,12 @@ class Hierarchy:
 # ----------------------------------------------------------------------------
 # Error norms (Sec. 7.2: discrete L2; readings in the design notes)
 # ----------------------------------------------------------------------------
+
+
+def mg_rate(hist, i_star=10, i0=5):
+    """Asymptotic convergence rate of Sec. 7 (start of the numerical section):
+    rho = (r^(i*) / r^(5))^(1 / (i* - 5))."""
+    return (hist[i_star] / hist[i0]) ** (1.0 / (i_star - i0))
 
 
 def discrete_l2(lm: LevelMesh, e):

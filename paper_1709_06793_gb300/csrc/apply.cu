@@ -968,6 +968,138 @@ static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk,
 }
 
 // ---------------------------------------------------------------------------
+// Diagonal of the nodal-integration operator: sum over the micro tets at a
+// node of kbar_t A_t[x][x] = -kbar_t sum_{w != x} A_t[x][w] (zero row sums),
+// summed over the copies of interface nodes; written as 1/diag, 0 on
+// Dirichlet nodes (Jacobi then leaves them unchanged).
+// ---------------------------------------------------------------------------
+template <class T, class KT>
+__device__ __forceinline__ T nodal_diag_partial(const TetDev& td, const T* __restrict__ elem, int i, int j, int k,
+                                                const KT* __restrict__ kk, bool check) {
+  const int N = td.N;
+  const T kx = (T)ldk(kk, td.base + node_offset(N, i, j, k));
+  T dg = 0;
+  for (int e = 0; e < 24; ++e) {
+    const NodalEntry& E = kNodal.e[e];
+    bool ok = true;
+    T ksum = 0, asum = 0;
+    const T* A = elem + E.sigma * 16 + E.v * 4;
+    for (int q = 0; q < 4; ++q) {
+      const int a = i + E.off[q][0], b = j + E.off[q][1], c = k + E.off[q][2];
+      if (check && (a < 0 || b < 0 || c < 0 || a + b + c > N)) ok = false;
+      if (!ok) break;
+      if (q == E.v) {
+        ksum += kx;
+      } else {
+        ksum += (T)ldk(kk, td.base + node_offset(N, a, b, c));
+        asum += A[q];
+      }
+    }
+    if (ok) dg -= ksum * asum;
+  }
+  return dg;
+}
+
+template <class T, class KT>
+__global__ void nodal_dinv_kernel(DepthDev D, const KT* __restrict__ kk, T* __restrict__ dinv) {
+  const T* elem;
+  if constexpr (sizeof(T) == 8)
+    elem = reinterpret_cast<const T*>(D.elem64);
+  else
+    elem = reinterpret_cast<const T*>(D.elem32);
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < D.n_rows; r += nwarps) {  // volume nodes
+    const int4 row = D.rows[r];
+    const TetDev td = D.tets[row.x];
+    const int N = td.N, j = row.y, k = row.z;
+    if (j == 0 || k == 0 || j + k >= N - 1) continue;
+    for (int i = 1 + lane; i + j + k <= N - 1; i += 32)
+      dinv[td.base + node_offset(N, i, j, k)] = (T)1 / nodal_diag_partial<T, KT>(td, elem + row.x * 96, i, j, k, kk, false);
+  }
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.n_bnodes; b += gridDim.x * blockDim.x) {
+    const int lo = D.bstart[b], hi = D.bstart[b + 1];
+    T v = 0;
+    if (!D.bdir[b]) {
+      T dg = 0;
+      for (int q = lo; q < hi; ++q) {
+        const BCopy cp = D.bcopies[q];
+        dg += nodal_diag_partial<T, KT>(D.tets[cp.slot], elem + cp.slot * 96, cp.i, cp.j, cp.k, kk, true);
+      }
+      v = (T)1 / dg;
+    }
+    for (int q = lo; q < hi; ++q) dinv[D.bcopies[q].idx] = v;
+  }
+}
+
+// residual / Jacobi / diagonal epilogue of the nodal operator from y = A_n u
+template <class T, int MODE>
+__global__ void nodal_epilogue_kernel(const T* __restrict__ y, const T* __restrict__ u, const T* __restrict__ f,
+                                      const T* __restrict__ dinv, T* __restrict__ out, double omega, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const bool dir = dinv[i] == (T)0;
+    if (MODE == OP_RESID) {
+      out[i] = dir ? (T)0 : f[i] - y[i];
+    } else if (MODE == OP_JACOBI) {
+      out[i] = dir ? (T)0 : u[i] + (T)omega * (f[i] - y[i]) * dinv[i];
+    } else {  // OP_DIAG
+      out[i] = dir ? (T)1 : (T)1 / dinv[i];
+    }
+  }
+}
+
+template <class T, class KT>
+static void nodal_dinv_typed(const Mesh& m, int depth, const void* kk, void* dinv, cudaStream_t s) {
+  const DepthDev& D = m.depth[depth].dev;
+  const int g = std::max(1, std::min(8 * m.num_sms, std::max((D.n_rows + 7) / 8, (D.n_bnodes + 255) / 256)));
+  nodal_dinv_kernel<T, KT><<<g, 256, 0, s>>>(D, static_cast<const KT*>(kk), static_cast<T*>(dinv));
+  HHG_CUDA(cudaGetLastError());
+}
+
+void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s) {
+  const Depth& Dh = m.depth[depth];
+  if (dtype == HHG_F64)
+    nodal_dinv_typed<double, double>(m, depth, Dh.k64, dinv, s);
+  else if (dtype == kF64KBF16)
+    nodal_dinv_typed<double, double>(m, depth, Dh.k16d, dinv, s);
+  else if (dtype == HHG_F32)
+    nodal_dinv_typed<float, float>(m, depth, Dh.k32, dinv, s);
+  else
+    nodal_dinv_typed<float, __nv_bfloat16>(m, depth, Dh.k16, dinv, s);
+}
+
+// Nodal-integration operator with the scaled kernel's modes: y = A_n u into
+// `tmp` (the fast staged kernels), then the pointwise epilogue with 1/diag.
+void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, const void* dinv, void* tmp,
+                     cudaStream_t s) {
+  HHG_REQUIRE(mode == OP_APPLY || mode == OP_RESID || mode == OP_JACOBI || mode == OP_DIAG,
+              "the nodal operator has no Chebyshev mode");
+  const long long n = a.nc_only ? m.depth[depth].n_stored_nc : m.depth[depth].n_stored;
+  if (mode == OP_APPLY) {
+    launch_nodal_apply(m, depth, dtype, a.u, a.out, s);
+    return;
+  }
+  if (mode != OP_DIAG) launch_nodal_apply(m, depth, dtype, a.u, tmp, s);
+  if (n == 0) return;
+  const int g = (int)std::min<long long>((n + 255) / 256, 8LL * m.num_sms);
+  const bool f64 = dtype == HHG_F64 || dtype == kF64KBF16;
+#define HHG_EPI(T, MD)                                                                                          \
+  nodal_epilogue_kernel<T, MD><<<g, 256, 0, s>>>(static_cast<const T*>(tmp), static_cast<const T*>(a.u),      \
+                                                 static_cast<const T*>(a.f), static_cast<const T*>(dinv),     \
+                                                 static_cast<T*>(a.out), a.omega, n)
+  if (mode == OP_RESID) {
+    if (f64) HHG_EPI(double, OP_RESID); else HHG_EPI(float, OP_RESID);
+  } else if (mode == OP_JACOBI) {
+    if (f64) HHG_EPI(double, OP_JACOBI); else HHG_EPI(float, OP_JACOBI);
+  } else {
+    if (f64) HHG_EPI(double, OP_DIAG); else HHG_EPI(float, OP_DIAG);
+  }
+#undef HHG_EPI
+  HHG_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
 // "Scale Vol+Face" (Sec. 5, eq. "modst" with I = W_V u W_E): after the scaled
 // launch, the rows of nodes on macro vertices and edges (face mask with two or
 // more bits in every containing tet) are replaced by their nodal-integration

@@ -126,7 +126,9 @@ struct Depth {
   // multigrid workspace per precision (allocated lazily): 0 = f64, 1 = f32
   // slots: 0 F (depth>0) / CG r (depth 0), 1 U / CG z, 2 V-cycle residual,
   // 3 CG p, 4 smoother ping-pong, 5-6 Chebyshev updates, 7 CG q, 8 inner solution
-  void* ws[2][10] = {{nullptr}};
+  // 9 inner solution, 10 operator scratch (nodal modes), 11 spare
+  void* ws[2][12] = {{nullptr}};
+  void* ndinv[4] = {nullptr, nullptr, nullptr, nullptr};  // nodal operator 1/diag per dtype (0 on Dirichlet)
   int* cslot_map = nullptr;  // slot at depth+1 of each slot (prolongation)
   double lam = 0.0;  // lambda_max of D^-1 A (FP64, 0 = not yet estimated)
 };
@@ -163,8 +165,12 @@ struct Mesh {
   int* d_ccopies_off = nullptr;
   bool device = true;            // false: host-only inspection mesh
   bool coef_set = false;
-  bool cinv_ready[4] = {false, false, false, false};  // per dtype
-  double* d_cinv[4] = {nullptr, nullptr, nullptr, nullptr};  // dense coarse inverses (packed)
+  // operator of the multigrid internals (V-cycle, smoothers, residuals, coarse
+  // solve): 0 scaled, 1 "scale Vol+Face", 2 nodal integration; set by the
+  // multigrid solve for its duration, 0 otherwise
+  int opk = 0;
+  bool cinv_ready[3][4] = {};         // per operator and dtype
+  double* d_cinv[3][4] = {};          // dense coarse inverses (packed)
   std::vector<long long> cinv_off;  // per component offset into d_cinv
   // scratch
   double* d_red = nullptr;        // reduction partials
@@ -247,6 +253,10 @@ void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const Op
 void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 // scaled launch followed by the nodal-integration rows of macro vertices and edges (eq. "modst")
 void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
+// nodal-integration operator in the modes above (dinv: 1/diag, 0 on Dirichlet nodes; tmp: a scratch vector)
+void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s);
+void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, const void* dinv, void* tmp,
+                     cudaStream_t s);
 void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 
 }  // namespace hhg

@@ -95,7 +95,13 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
     HHG_CUDA(cudaGetLastError());
   }
   m.coef_set = true;
-  for (int t = 0; t < 4; ++t) m.cinv_ready[t] = false;
+  for (int o = 0; o < 3; ++o)
+    for (int t = 0; t < 4; ++t) m.cinv_ready[o][t] = false;
+  for (Depth& D : m.depth)
+    for (int t = 0; t < 4; ++t)
+      if (D.ndinv[t]) {
+        D.ndinv[t] = nullptr;  // recomputed on next use (the memory stays with the depth)
+      }
   for (int d = 0; d < m.ndepth; ++d) m.depth[d].lam = 0.0;
 }
 
@@ -432,8 +438,10 @@ static void host_cholesky_inverse(std::vector<double>& A, int n) {
   A.swap(X);
 }
 
+static void coarse_by_columns(Mesh& m, std::vector<double>& all, std::vector<long long>& off, cudaStream_t s);
+
 void ensure_coarse(Mesh& m, int dtype, cudaStream_t s) {
-  if (m.cinv_ready[dtype]) return;
+  if (m.cinv_ready[m.opk][dtype]) return;
   HHG_CUDA(cudaStreamSynchronize(s));
   Depth& D0 = m.depth[0];
   // index arrays (once)
@@ -466,7 +474,8 @@ void ensure_coarse(Mesh& m, int dtype, cudaStream_t s) {
   // assemble each component's coarse matrix with the coefficient of this dtype
   std::vector<double> all;
   std::vector<long long> off;
-  for (int c = 0; c < m.ncomp; ++c) {
+  if (m.opk != 0) coarse_by_columns(m, all, off, s);
+  for (int c = 0; c < m.ncomp && m.opk == 0; ++c) {
     const CoarseComp& C = m.coarse[c];
     const Depth& D = m.depth[C.depth];
     std::vector<double> k(D.n_stored);
@@ -525,18 +534,19 @@ void ensure_coarse(Mesh& m, int dtype, cudaStream_t s) {
     off.push_back((long long)all.size());
     all.insert(all.end(), A.begin(), A.end());
   }
-  if (!m.d_cinv[dtype]) m.d_cinv[dtype] = static_cast<double*>(dalloc(D0, std::max<size_t>(all.size(), 1) * 8));
-  HHG_CUDA(cudaMemcpy(m.d_cinv[dtype], all.data(), all.size() * 8, cudaMemcpyHostToDevice));
+  double*& cinv = m.d_cinv[m.opk][dtype];
+  if (!cinv) cinv = static_cast<double*>(dalloc(D0, std::max<size_t>(all.size(), 1) * 8));
+  HHG_CUDA(cudaMemcpy(cinv, all.data(), all.size() * 8, cudaMemcpyHostToDevice));
   if (!m.d_cinv_off) m.d_cinv_off = static_cast<long long*>(dalloc(D0, std::max<size_t>(off.size(), 1) * 8));
   HHG_CUDA(cudaMemcpy(m.d_cinv_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
-  m.cinv_ready[dtype] = true;
+  m.cinv_ready[m.opk][dtype] = true;
 }
 
 // u = A_c^-1 f for every component at its coarse depth; f, u given per depth.
 // ensure_coarse() must have run (it synchronises); this only enqueues work.
 void coarse_solve(Mesh& m, int dtype, void* const* fdepth, void* const* udepth, cudaStream_t s) {
   const int kd = dtype == kF64KBF16 ? (int)HHG_F32_KBF16 : dtype;
-  HHG_REQUIRE(m.cinv_ready[kd], "internal: coarse inverse not prepared");
+  HHG_REQUIRE(m.cinv_ready[m.opk][kd], "internal: coarse inverse not prepared");
   DepthPtrs P{};
   for (int d = 0; d < m.ndepth; ++d) {
     P.f[d] = fdepth[d];
@@ -548,12 +558,12 @@ void coarse_solve(Mesh& m, int dtype, void* const* fdepth, void* const* udepth, 
   if (elem_size(dtype) == 8) {
     if (shm > 48 * 1024)
       HHG_CUDA(cudaFuncSetAttribute(coarse_apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    coarse_apply_kernel<double><<<m.ncomp, 256, shm, s>>>(m.d_cinv[kd], m.d_cinv_off, m.d_cn, m.d_cdepth, m.d_crep,
+    coarse_apply_kernel<double><<<m.ncomp, 256, shm, s>>>(m.d_cinv[m.opk][kd], m.d_cinv_off, m.d_cn, m.d_cdepth, m.d_crep,
                                                          m.d_crep_off, m.d_ccstart, m.d_ccopies, m.d_ccopies_off, P);
   } else {
     if (shm > 48 * 1024)
       HHG_CUDA(cudaFuncSetAttribute(coarse_apply_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    coarse_apply_kernel<float><<<m.ncomp, 256, shm, s>>>(m.d_cinv[kd], m.d_cinv_off, m.d_cn, m.d_cdepth, m.d_crep,
+    coarse_apply_kernel<float><<<m.ncomp, 256, shm, s>>>(m.d_cinv[m.opk][kd], m.d_cinv_off, m.d_cn, m.d_cdepth, m.d_crep,
                                                         m.d_crep_off, m.d_ccstart, m.d_ccopies, m.d_ccopies_off, P);
   }
   HHG_CUDA(cudaGetLastError());
@@ -562,10 +572,85 @@ void coarse_solve(Mesh& m, int dtype, void* const* fdepth, void* const* udepth, 
 // ---------------------------------------------------------------------------
 // operator helpers
 // ---------------------------------------------------------------------------
+// 1/diag of the nodal operator at a depth (computed once per coefficient)
+const void* nodal_dinv(Mesh& m, int depth, int dtype, cudaStream_t s) {
+  Depth& D = m.depth[depth];
+  if (!D.ndinv[dtype]) {
+    void* p = workspace(m, depth, prec_of(dtype), 11);
+    for (int t = 0; t < 4; ++t)  // dtypes of one precision share the buffer
+      if (prec_of(t) == prec_of(dtype)) D.ndinv[t] = nullptr;
+    launch_nodal_dinv(m, depth, dtype, p, s);
+    D.ndinv[dtype] = p;
+  }
+  return D.ndinv[dtype];
+}
+
+// one operator launch in the given mode, with the operator of m.opk
 static void op(Mesh& m, int depth, int dtype, OpMode mode, const void* u, const void* f, void* out, const void* din,
                void* dout, double omega, double ca, double cb, bool nc_only, cudaStream_t s) {
   OpArgs a{u, f, out, din, dout, omega, ca, cb, nc_only ? 1 : 0};
-  launch_scaled_op(m, depth, dtype, mode, a, s);
+  if (m.opk == 1)
+    launch_volface_op(m, depth, dtype, mode, a, s);
+  else if (m.opk == 2)
+    launch_nodal_op(m, depth, dtype, mode, a, nodal_dinv(m, depth, dtype, s), workspace(m, depth, prec_of(dtype), 10),
+                    s);
+  else
+    launch_scaled_op(m, depth, dtype, mode, a, s);
+}
+
+// Coarse matrices of a non-scaled operator, column by column: the operator
+// applied (FP64, on the GPU) to the unit vector of each coarse unknown, then
+// inverted by Gauss-Jordan elimination with partial pivoting (the Vol+Face
+// operator is not symmetric).
+static void coarse_by_columns(Mesh& m, std::vector<double>& all, std::vector<long long>& off, cudaStream_t s) {
+  for (int c = 0; c < m.ncomp; ++c) {
+    const CoarseComp& C = m.coarse[c];
+    const int d = C.depth;
+    const long long ns = m.depth[d].n_stored;
+    const int n = C.n;
+    double* e = static_cast<double*>(workspace(m, d, 0, 9));
+    double* y = static_cast<double*>(workspace(m, d, 0, 10));
+    std::vector<double> A((size_t)n * n, 0.0), eh(ns, 0.0), yh(ns);
+    for (int u = 0; u < n; ++u) {
+      for (int q = C.h_cstart[u]; q < C.h_cstart[u + 1]; ++q) eh[C.h_copies[q]] = 1.0;
+      HHG_CUDA(cudaMemcpyAsync(e, eh.data(), ns * 8, cudaMemcpyHostToDevice, s));
+      op(m, d, HHG_F64, OP_APPLY, e, nullptr, y, nullptr, nullptr, 0, 0, 0, false, s);
+      HHG_CUDA(cudaMemcpyAsync(yh.data(), y, ns * 8, cudaMemcpyDeviceToHost, s));
+      HHG_CUDA(cudaStreamSynchronize(s));
+      for (int v = 0; v < n; ++v) A[(size_t)v * n + u] = yh[C.h_rep[v]];
+      for (int q = C.h_cstart[u]; q < C.h_cstart[u + 1]; ++q) eh[C.h_copies[q]] = 0.0;
+    }
+    // Gauss-Jordan with partial pivoting: A <- A^-1
+    std::vector<double> I((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    for (int col = 0; col < n; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < n; ++r)
+        if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+      HHG_REQUIRE(A[(size_t)piv * n + col] != 0.0, "singular coarse matrix");
+      if (piv != col)
+        for (int j = 0; j < n; ++j) {
+          std::swap(A[(size_t)piv * n + j], A[(size_t)col * n + j]);
+          std::swap(I[(size_t)piv * n + j], I[(size_t)col * n + j]);
+        }
+      const double inv = 1.0 / A[(size_t)col * n + col];
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)col * n + j] *= inv;
+        I[(size_t)col * n + j] *= inv;
+      }
+      for (int r = 0; r < n; ++r) {
+        if (r == col) continue;
+        const double fct = A[(size_t)r * n + col];
+        if (fct == 0.0) continue;
+        for (int j = 0; j < n; ++j) {
+          A[(size_t)r * n + j] -= fct * A[(size_t)col * n + j];
+          I[(size_t)r * n + j] -= fct * I[(size_t)col * n + j];
+        }
+      }
+    }
+    off.push_back((long long)all.size());
+    all.insert(all.end(), I.begin(), I.end());
+  }
 }
 
 void apply_scaled(Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s) {

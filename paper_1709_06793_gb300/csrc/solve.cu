@@ -21,6 +21,7 @@ void init_launch_configs(int dtype);
 void learned_prepare(Mesh& m, int dtype, cudaStream_t s);
 bool learned_accepted(Mesh& m);
 void random_vector(Mesh& m, int d, float* x, unsigned long long key, cudaStream_t s);
+const void* nodal_dinv(Mesh& m, int depth, int dtype, cudaStream_t s);
 
 enum { RED_STORE = 0, RED_ALPHA = 1, RED_BETA = 2, RED_FBETA = 3 };
 
@@ -69,11 +70,14 @@ void drop_graphs(Mesh& m) {
 // that afterwards the iteration only enqueues kernels (capturable).
 void prepare(Mesh& m, int dtype, int smoother, cudaStream_t s) {
   HHG_REQUIRE(m.coef_set, "hhg_set_coefficient must be called first");
+  HHG_REQUIRE(m.opk == 0 || smoother == HHG_SMOOTH_JACOBI,
+              "the Vol+Face and nodal operators are smoothed with damped Jacobi");
   const int pr = prec_of(dtype);
   init_launch_configs(dtype);
   init_launch_configs(HHG_F64);
   for (int d = 0; d < m.ndepth; ++d) {
     for (int w : {0, 1, 2, 3, 4, 5, 6, 7, 8}) workspace(m, d, pr, w);
+    if (m.opk == 2) nodal_dinv(m, d, dtype, s);
     if (d + 1 < m.ndepth) coarse_slot_map(m, d);
   }
   if (smoother == HHG_SMOOTH_CHEBYSHEV)
@@ -199,6 +203,56 @@ double pcg_rate(Mesh& m, int dtype, int smoother, int nu1, int nu2, double omega
   return std::pow(res.rr / rr0, 0.5 / res.its);
 }
 
+// Multigrid as the solver (Sec. 7.2): u <- V(nu1,nu2)(f, u) in FP64 with the
+// operator p.op until ||f - A u|| <= tol ||f|| or p.maxit cycles; rho as in
+// Sec. 7, (r^(i*) / r^(5))^(1/(i*-5)) (from r^(0) when i* <= 5).
+static int solve_mg(Mesh& m, const hhg_solve_params& p, const double* f, double* u, hhg_solve_stats* st,
+                    cudaStream_t s) {
+  HHG_REQUIRE(p.smoother == HHG_SMOOTH_JACOBI || (p.smoother == HHG_SMOOTH_CHEBYSHEV && p.op == 0),
+              "multigrid solve: Jacobi smoothing (Chebyshev for the scaled operator only)");
+  const auto t0 = std::chrono::steady_clock::now();
+  struct OpGuard {  // the multigrid internals use p.op for this call only
+    Mesh& m;
+    OpGuard(Mesh& mm, int opk) : m(mm) {
+      drop_graphs(m);
+      m.opk = opk;
+    }
+    ~OpGuard() { m.opk = 0; }
+  } guard(m, p.op);
+  prepare(m, HHG_F64, p.smoother, s);
+  double* r = static_cast<double*>(workspace(m, 0, 0, 8));
+  dot(m, 0, HHG_F64, f, f, 6, RED_STORE, false, s);
+  const double nf = std::sqrt(read_scalar(m, 6, s));
+  std::vector<double> hist;
+  residual(m, 0, HHG_F64, f, u, r, false, s);
+  dot(m, 0, HHG_F64, r, r, 7, RED_STORE, false, s);
+  hist.push_back(std::sqrt(read_scalar(m, 7, s)));
+  int it = 0;
+  while (it < p.maxit && nf > 0 && hist.back() > p.tol * nf && std::isfinite(hist.back())) {
+    vcycle(m, HHG_F64, p.nu1, p.nu2, p.smoother, p.omega, f, u, s);
+    residual(m, 0, HHG_F64, f, u, r, false, s);
+    dot(m, 0, HHG_F64, r, r, 7, RED_STORE, false, s);
+    hist.push_back(std::sqrt(read_scalar(m, 7, s)));
+    ++it;
+  }
+  HHG_CUDA(cudaStreamSynchronize(s));
+  const double rel = nf > 0 ? hist.back() / nf : 0.0;
+  double rho = 0.0;
+  if (it > 5 && hist[5] > 0)
+    rho = std::pow(hist[it] / hist[5], 1.0 / (it - 5));
+  else if (it > 0 && hist[0] > 0)
+    rho = std::pow(hist[it] / hist[0], 1.0 / it);
+  if (st) {
+    st->iterations = it;
+    st->outer = 1;
+    st->rel_residual = rel;
+    st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    st->smoother_used = p.smoother;
+    st->rho = rho;
+  }
+  return rel <= p.tol ? HHG_OK : HHG_ERR_NOT_CONVERGED;
+}
+
 int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s) {
   hhg_solve_params p = p_in;
   if (p.omega <= 0) p.omega = 2.0 / 3.0;
@@ -206,7 +260,10 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
   if (p.max_outer <= 0) p.max_outer = 20;
   if (p.maxit <= 0) p.maxit = 200;
   HHG_REQUIRE(p.tol > 0, "tol must be positive");
-  HHG_REQUIRE(p.mode >= 0 && p.mode <= 2, "unknown solve mode");
+  HHG_REQUIRE(p.mode >= 0 && p.mode <= 3, "unknown solve mode");
+  HHG_REQUIRE(p.op >= 0 && p.op <= 2, "unknown operator");
+  HHG_REQUIRE(p.op == 0 || p.mode == HHG_SOLVE_MG, "the Vol+Face and nodal operators are solved with HHG_SOLVE_MG");
+  if (p.mode == HHG_SOLVE_MG) return solve_mg(m, p, f, u, st, s);
   const auto t0 = std::chrono::steady_clock::now();
   const long long n = m.depth[0].n_stored;
   const int g = grid_for(n, 256, 8 * m.num_sms);
@@ -279,6 +336,7 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
     st->rel_residual = rel;
     st->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     st->smoother_used = p.smoother;
+    st->rho = 0.0;
   }
   return status;
 }

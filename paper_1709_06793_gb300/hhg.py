@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libhhg.so")
 
 HHG_F64, HHG_F32, HHG_F32_KBF16 = 0, 1, 2
 HHG_SMOOTH_JACOBI, HHG_SMOOTH_CHEBYSHEV, HHG_SMOOTH_LEARNED = 0, 1, 2
-HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16 = 0, 1, 2
+HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16, HHG_SOLVE_MG = 0, 1, 2, 3
+HHG_OP_SCALED, HHG_OP_VOLFACE, HHG_OP_NODAL = 0, 1, 2
 STATUS = {0: "HHG_OK", -1: "HHG_ERR_ARG", -2: "HHG_ERR_CUDA", -3: "HHG_ERR_NOMEM",
           -4: "HHG_ERR_NOT_CONVERGED", -5: "HHG_ERR_TIMEOUT", -6: "HHG_ERR_STATE"}
 
@@ -32,12 +33,12 @@ class HHGError(RuntimeError):
 class SolveParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("mode", C.c_int), ("smoother", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double), ("inner_rtol", C.c_double),
-                ("max_outer", C.c_int), ("use_graph", C.c_int)]
+                ("max_outer", C.c_int), ("use_graph", C.c_int), ("op", C.c_int)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("rel_residual", C.c_double),
-                ("time_ms", C.c_double), ("smoother_used", C.c_int)]
+                ("time_ms", C.c_double), ("smoother_used", C.c_int), ("rho", C.c_double)]
 
 
 class LearnParams(C.Structure):
@@ -251,14 +252,16 @@ def hhg_dot(mesh, depth, x, y, dtype, stream=None):
 
 
 def hhg_solve(mesh, f, u, tol=1e-8, maxit=200, mode=HHG_SOLVE_FP64, smoother=HHG_SMOOTH_JACOBI, nu1=2, nu2=2,
-              omega=2.0 / 3.0, inner_rtol=1e-4, max_outer=20, use_graph=1, stream=None, raise_on_fail=True):
-    p = SolveParams(tol, maxit, mode, smoother, nu1, nu2, omega, inner_rtol, max_outer, use_graph)
+              omega=2.0 / 3.0, inner_rtol=1e-4, max_outer=20, use_graph=1, stream=None, raise_on_fail=True,
+              op=HHG_OP_SCALED):
+    p = SolveParams(tol, maxit, mode, smoother, nu1, nu2, omega, inner_rtol, max_outer, use_graph, op)
     st = SolveStats()
     code = _lib.hhg_solve(mesh, C.byref(p), _ptr(f), _ptr(u), C.byref(st), _stream(stream))
     if code != 0 and (raise_on_fail or code != -4):
         _check(code)
     return {"iterations": st.iterations, "outer": st.outer, "rel_residual": st.rel_residual,
-            "time_ms": st.time_ms, "smoother_used": st.smoother_used, "status": STATUS.get(code, code)}
+            "time_ms": st.time_ms, "smoother_used": st.smoother_used, "rho": st.rho,
+            "status": STATUS.get(code, code)}
 
 
 def hhg_learned_train(mesh, steps=150, pairs=4, lr=3e-3, omega=2.0 / 3.0, max_depth=0, vcycle_pairs=0,

@@ -195,6 +195,32 @@ def f_cube_sine(x):
     return -(np.sum(gk * gu, axis=1) + k_cube(x) * (-3.0 * np.pi ** 2) * u_sine(x))
 
 
+def k_cosine(m):
+    """k = cos(m pi x y z) + 2 (the parameter-dependent coefficient of the
+    paper's 3D scalar test, Sec. 7.2, m = 3 and 8)."""
+
+    def k(x):
+        x = np.asarray(x, dtype=np.float64)
+        return np.cos(m * np.pi * x[:, 0] * x[:, 1] * x[:, 2]) + 2.0
+
+    return k
+
+
+def f_sine_cosine_k(m):
+    """f = -div(k grad u) for k = k_cosine(m) and u = u_sine (zero on the
+    cube's boundary)."""
+
+    def f(x):
+        x = np.asarray(x, dtype=np.float64)
+        p = x[:, 0] * x[:, 1] * x[:, 2]
+        s = -m * np.pi * np.sin(m * np.pi * p)
+        gk = np.stack([s * x[:, 1] * x[:, 2], s * x[:, 0] * x[:, 2], s * x[:, 0] * x[:, 1]], axis=1)
+        k = np.cos(m * np.pi * p) + 2.0
+        return -(np.sum(gk * grad_u_sine(x), axis=1) + k * (-3.0 * np.pi ** 2) * u_sine(x))
+
+    return f
+
+
 def k_large(x):
     """1 + 0.5 sin(4 pi x) cos(4 pi y) sin(4 pi z)."""
     x = np.asarray(x, dtype=np.float64)

@@ -426,3 +426,39 @@ def test_chebyshev_solve(H, mode):
 
 def test_device_status_clean(H, case):
     H.hhg_device_status(case.m.h)  # raises on a recorded timeout
+
+
+@pytest.mark.parametrize("kind,op", [("scaled", 0), ("volface", 1), ("nodal", 2)])
+@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3"])
+def test_mg_solver_parity(H, name, kind, op):
+    """HHG_SOLVE_MG (FP64 V(3,3) cycles as the solver) with each operator
+    against the oracle hierarchy of the same operator: the iterate after 3
+    cycles (1e-10) and the rate rho over 10 cycles."""
+    mesh, level, coarsest, kf = MESHES[name]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    Ho = O.Hierarchy(V, T, level, coarsest, k_func=kf, kind=kind)
+    f_or = c.rand_or
+    fu = f_or[c.lm.unknowns]
+    for its in (3, 10):
+        u = torch.zeros(c.n, device="cuda", dtype=torch.float64)
+        st = H.hhg_solve(c.m.h, c.dev(f_or, 0), u, tol=1e-30, maxit=its, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3,
+                         op=op, raise_on_fail=False)
+        assert st["iterations"] == its
+        x, hist = Ho.mg_solve(fu, its)
+        got = c.back(u)[c.lm.unknowns]
+        assert _rel(got, x) <= 1e-10, _rel(got, x)
+        if its == 10:
+            assert abs(st["rho"] - O.mg_rate(hist)) <= 1e-6 * O.mg_rate(hist)
+            assert 0 < st["rho"] < 0.5
+    c.m.close()
+
+
+def test_mg_solver_rejects_operator_outside_mg_mode(H):
+    mesh, level, coarsest, kf = MESHES["kuhn_cube_l4"]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    u = torch.zeros(c.n, device="cuda", dtype=torch.float64)
+    with pytest.raises(H.HHGError, match="HHG_SOLVE_MG"):
+        H.hhg_solve(c.m.h, c.dev(c.rand_or, 0), u, mode=H.HHG_SOLVE_FP64, op=H.HHG_OP_VOLFACE)
+    c.m.close()
