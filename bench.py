@@ -253,6 +253,54 @@ def learned_bench(H, I, torch, stream, flush):
     return out
 
 
+TABLE_LEVELS = (4, 5, 6, 7, 8)  # the paper's L = 2 .. 6 on the 6-tet cube
+
+
+def paper_table(H, I, torch, m_big=None, levels=TABLE_LEVELS):
+    """Shape of the paper's 3D scalar table (Sec. 7.2, Tab. "hhg_nonlinear",
+    m = 3): 10 V(3,3) multigrid cycles in FP64 with nodal integration,
+    scale Vol+Face and scale all; discrete L2 error (lumped mass) of the
+    manufactured u = sin(pi x) sin(pi y) sin(pi z), eoc, rho and the time to
+    solution relative to nodal integration.  Coefficient k = cos(3 pi x y z) + 2."""
+    rows = []
+    prev = {}
+    kf, ff = I.k_cosine(3), I.f_sine_cosine_k(3)
+    V, T = I.kuhn_cube()
+    for level in levels:
+        m = m_big if (m_big is not None and level == LEVEL) else H.Mesh(V, T, level, COARSEST)
+        off, lev, n = m.layout(0)
+        xyz = m.coords(0)
+        H.hhg_set_coefficient(m.h, torch.tensor(kf(xyz), device="cuda"))
+        fi = torch.tensor(ff(xyz), device="cuda")
+        f = torch.empty_like(fi)
+        H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
+        w = torch.empty_like(fi)
+        H.hhg_apply_mass(m.h, 0, torch.ones_like(fi), w, H.HHG_F64)  # lumped mass weights
+        ustar = torch.tensor(I.u_sine(xyz), device="cuda")
+        row = {"level": level, "L": level - 2, "unknowns": ((1 << level) - 1) ** 3}
+        for name, op in (("nodal", H.HHG_OP_NODAL), ("volface", H.HHG_OP_VOLFACE), ("scaled", H.HHG_OP_SCALED)):
+            u = torch.zeros(n, device="cuda", dtype=torch.float64)
+            H.hhg_solve(m.h, f, u, tol=1e-30, maxit=10, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3, op=op,
+                        raise_on_fail=False)  # warm: coarse inverse, diagonals
+            u.zero_()
+            torch.cuda.synchronize()
+            st = H.hhg_solve(m.h, f, u, tol=1e-30, maxit=10, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3, op=op,
+                             raise_on_fail=False)
+            e = u - ustar
+            err = math.sqrt(max(H.hhg_dot(m.h, 0, w * e, e, H.HHG_F64), 0.0))
+            eoc = math.log2(prev[name] / err) if name in prev else None
+            prev[name] = err
+            row[name] = {"error": err, "eoc": eoc, "rho": st["rho"], "tts_ms": st["time_ms"]}
+        for name in ("volface", "scaled"):
+            row[name]["rel_tts"] = row[name]["tts_ms"] / row["nodal"]["tts_ms"]
+        rows.append(row)
+        if m is not m_big:
+            m.close()
+    return {"workload": "unit cube, 6 Kuhn macro-tets, k = cos(3 pi x y z) + 2, u* = sin(pi x) sin(pi y) sin(pi z), "
+                        "rhs M I_h f; 10 V(3,3) cycles (damped Jacobi, omega 2/3), FP64",
+            "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +311,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the multigrid table (nodal / Vol+Face / scaled)")
     ap.add_argument("--only-learned", action="store_true",
                     help="run only the learned-smoother section (C4) and print its JSON")
     ap.add_argument("--tune-cache", action="store_true", help="reuse/append autotuner results in _build_tune.txt")
@@ -385,6 +434,10 @@ def main():
                            "rhs M I_h f; FP64 outer residual in every mode")
         solve["speedup_mixed_vs_fp64"] = solve["fp64"]["ms"] / solve["mixed_fp32_fp64refine"]["ms"]
 
+    table = None
+    if not args.no_table:
+        table = paper_table(H, I, torch, m_big=m)
+
     learned = None
     if not args.no_learned:
         learned = learned_bench(H, I, torch, stream, flush)
@@ -401,7 +454,7 @@ def main():
                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
            "autotune": tune,
-           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve, "learned": learned}
+           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve, "learned": learned, "mg_table": table}
     if rank == 0:
         print(json.dumps(out))
     m.close()
