@@ -279,9 +279,29 @@ static int find(std::vector<int>& p, int x) {
 // Volume work list: tiles of kTI x kTJ columns (i0, j0), 4 per warp item (one
 // tet per item, equal i0+j0 where possible), each tile's k-march cut into
 // segments of m.kseg planes; longest item first.
+// k-segment length of a depth: the mesh's kseg, halved (down to 4) while the
+// depth would have fewer volume items than resident warps (16 per SM), so
+// that small depths still spread over the whole GPU
+static int depth_kseg(const Mesh& m, const Depth& D) {
+  const long long target = (long long)(m.num_sms > 0 ? m.num_sms : 152) * 16;
+  auto count = [&](int ks) {
+    long long c = 0;
+    for (size_t s = 0; s < D.h_tets.size(); ++s) {
+      const int N = D.h_tets[s].N;
+      for (int j0 = 1; j0 <= N - 2; j0 += kWarpTileJ)
+        for (int i0 = 1; i0 + j0 <= N - 2; i0 += kWarpTileI) c += (N - 1 - (i0 + j0) + ks - 1) / ks;
+    }
+    return c;
+  };
+  int ks = m.kseg;
+  while (ks > 4 && count(ks) < target) ks /= 2;
+  return ks;
+}
+
 void build_items(const Mesh& m, Depth& D) {
   const int ns = (int)D.slot_tet.size();
   const int empty_tile = 1023 << 10 | 1023;
+  const int kseg = depth_kseg(m, D);
   std::vector<std::vector<int4>> by_class(2);
   for (int cls = 0; cls < 2; ++cls) {
     std::vector<std::pair<long long, int4>> its;  // (sort key, item)
@@ -292,7 +312,7 @@ void build_items(const Mesh& m, Depth& D) {
         // quads: the 4 warps of a block take 4 tiles stacked in j (same i0,
         // same plane window), so the halo rows they share are fetched once
         const int jstack = 4 * kWarpTileJ;
-        for (int k0 = 1; k0 <= N - 3; k0 += m.kseg)
+        for (int k0 = 1; k0 <= N - 3; k0 += kseg)
           for (int jg = 1; jg <= N - 2; jg += jstack)
             for (int i0 = 1; i0 + jg <= N - 2; i0 += kWarpTileI) {
               int4 q[4];
@@ -301,7 +321,7 @@ void build_items(const Mesh& m, Depth& D) {
                 const int j0 = jg + w * kWarpTileJ;
                 const int top = N - 1 - (i0 + j0);
                 if (j0 <= N - 2 && top >= k0) {
-                  q[w] = make_int4(s << 20 | j0 << 10 | i0, k0, std::min(top, k0 + m.kseg - 1), 0);
+                  q[w] = make_int4(s << 20 | j0 << 10 | i0, k0, std::min(top, k0 + kseg - 1), 0);
                   ++live;
                 } else {
                   q[w] = make_int4(s << 20 | empty_tile, 1, 0, 0);  // no planes
@@ -316,8 +336,8 @@ void build_items(const Mesh& m, Depth& D) {
           for (int i0 = 1; i0 + j0 <= N - 2; i0 += kWarpTileI) {
             const int tile = s << 20 | j0 << 10 | i0;
             const int top = N - 1 - (i0 + j0);  // last plane with a volume node in the tile
-            for (int k0 = 1; k0 <= top; k0 += m.kseg) {
-              const int k1 = std::min(top, k0 + m.kseg - 1);
+            for (int k0 = 1; k0 <= top; k0 += kseg) {
+              const int k1 = std::min(top, k0 + kseg - 1);
               const long long key = m.korder == 1 ? k0 : -(long long)(k1 - k0 + 1);
               its.push_back({key, make_int4(tile, k0, k1, 0)});
             }
@@ -637,14 +657,16 @@ Mesh* build_mesh(const double* verts, int nv, const int* tets, int nt, const int
     for (int t = 0; t < nt; ++t) maxd = std::max(maxd, levels[t] - coarsest);
     m->ndepth = maxd + 1;
     m->depth.resize(m->ndepth);
+    if (device) {  // the SM count sizes the work lists
+      int dev = 0;
+      HHG_CUDA(cudaGetDevice(&dev));
+      HHG_CUDA(cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     for (int d = 0; d < m->ndepth; ++d) build_depth(*m, d);
     build_coarse(*m);
     m->device = device;
     if (!device) return m;
     for (int d = 0; d < m->ndepth; ++d) upload_depth(m->depth[d]);
-    int dev = 0;
-    HHG_CUDA(cudaGetDevice(&dev));
-    HHG_CUDA(cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev));
     Depth& D0 = m->depth[0];
     m->d_red = static_cast<double*>(dalloc(D0, 4096 * sizeof(double)));
     m->d_counter = static_cast<unsigned*>(dalloc(D0, 64 * sizeof(unsigned)));
