@@ -37,7 +37,9 @@ WORKLOAD = "unit cube, 6 Kuhn macro-tets, level 8 (257 nodes/edge), k=exp(sin(pi
 # ncu DRAM traffic (read+write bytes) per launch of the FP32 scaled apply on
 # this workload, with the sha256 of the kernel source it was measured on; the
 # figure is dropped (null) as soon as the kernel source changes.
-NCU_TRAFFIC = {"apply_sha": "293f99abcc244255", "bytes": 336677632}  # 271.88 MB read + 64.80 MB written
+# DRAM bytes of one apply (volume kernel 147.85 MB read + 35.93 MB written,
+# interface kernel 73.77 MB read + 5.65 MB written), one ncu capture each
+NCU_TRAFFIC = {"apply_sha": "f62ccbc1b5ffe6a6", "bytes": 263211264}
 
 
 def _kernel_sha():
@@ -407,7 +409,9 @@ def main():
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["apply_sha"] == _kernel_sha() else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"{src} hbm_gbs (burst)",
-            "kernel": "scaled_op_kernel<float,float,APPLY>", "algorithmic_bytes_per_launch": algo_bytes}
+            "kernel": "scaled_op_kernel<float,float,APPLY> (volume rows) + boundary_only_kernel<float,float,APPLY> "
+                      "(interface rows, concurrent on a side stream); one apply = one launch of each",
+            "algorithmic_bytes_per_launch": algo_bytes}
 
     solve = None
     if not args.no_solve:
@@ -452,7 +456,7 @@ def main():
            "config": {"workload": WORKLOAD, "level": args.level, "unknowns": unknowns, "stored_nodes": n,
                       "macro_tets": 6, "parallelism": f"replicas{world}" if world > 1 else "single",
                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
-           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
            "autotune": tune,
            "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve, "learned": learned, "mg_table": table}
     if rank == 0:

@@ -546,6 +546,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) scaled_op_kernel(
   }
 }
 
+// Interface rows on their own: one thread per unique interface node.  Runs on
+// the mesh's side stream concurrently with the volume kernel (its few
+// registers and no shared memory let it fill the warp slots the volume
+// kernel leaves free), instead of as chunks inside the volume kernel's loop.
+template <class T, class KT, int MODE>
+__global__ void __launch_bounds__(128) boundary_only_kernel(DepthDev D, OpPtrs p, int n_b) {
+  const T* sten;
+  if constexpr (sizeof(T) == 8)
+    sten = reinterpret_cast<const T*>(D.sten64);
+  else
+    sten = reinterpret_cast<const T*>(D.sten32);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += gridDim.x * blockDim.x)
+    boundary_node<T, KT, MODE>(D, sten, b, p);
+}
+
 template <class T, class KT>
 constexpr int ring_bytes() {
   return 4 * Stage<T, KT>::warp_bytes;  // 4 warps per block
@@ -592,8 +607,22 @@ static void launch_typed(const Mesh& m, int depth, const OpArgs& a, const void* 
   const int work = n_items + (n_b + 31) / 32;
   if (work == 0) return;
   const int occ = occupancy<T, KT, MODE>();
-  const int blocks = std::min((work + 3) / 4, m.num_sms * occ);
   OpPtrs p{a.u, kptr, a.f, a.out, a.d_in, a.d_out, a.omega, a.ca, a.cb};
+  if (n_items > 0 && n_b > 0 && m.side) {
+    // fork: interface rows on the side stream, volume rows here; join before
+    // returning (also valid inside a stream capture)
+    HHG_CUDA(cudaEventRecord(m.side_fork, s));
+    HHG_CUDA(cudaStreamWaitEvent(m.side, m.side_fork, 0));
+    boundary_only_kernel<T, KT, MODE><<<(n_b + 127) / 128, 128, 0, m.side>>>(D, p, n_b);
+    HHG_CUDA(cudaGetLastError());
+    HHG_CUDA(cudaEventRecord(m.side_join, m.side));
+    const int blocks = std::min((n_items + 3) / 4, m.num_sms * occ);
+    scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, 0, m.d_error);
+    HHG_CUDA(cudaGetLastError());
+    HHG_CUDA(cudaStreamWaitEvent(s, m.side_join, 0));
+    return;
+  }
+  const int blocks = std::min((work + 3) / 4, m.num_sms * occ);
   scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, n_b, m.d_error);
   HHG_CUDA(cudaGetLastError());
 }

@@ -180,6 +180,10 @@ struct Mesh {
   double* h_pinned = nullptr;     // pinned host scalars
   double* d_geom = nullptr;       // macro vertices (double) followed by tets (int)
   int num_sms = 0;
+  // side stream of the operator launches (interface rows concurrent with the
+  // volume kernel) and its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
   int cheb_degree = 2;
   double cheb_lo = 0.3, cheb_hi = 1.1;
   int power_its = 15;

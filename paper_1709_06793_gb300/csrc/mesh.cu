@@ -667,6 +667,9 @@ Mesh* build_mesh(const double* verts, int nv, const int* tets, int nt, const int
     m->device = device;
     if (!device) return m;
     for (int d = 0; d < m->ndepth; ++d) upload_depth(m->depth[d]);
+    HHG_CUDA(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    HHG_CUDA(cudaEventCreateWithFlags(&m->side_fork, cudaEventDisableTiming));
+    HHG_CUDA(cudaEventCreateWithFlags(&m->side_join, cudaEventDisableTiming));
     Depth& D0 = m->depth[0];
     m->d_red = static_cast<double*>(dalloc(D0, 4096 * sizeof(double)));
     m->d_counter = static_cast<unsigned*>(dalloc(D0, 64 * sizeof(unsigned)));
@@ -688,6 +691,12 @@ void free_mesh(Mesh* m) {
   if (!m) return;
   drop_graphs(*m);
   free_learned(m);
+  if (m->side) {
+    cudaStreamSynchronize(m->side);
+    cudaStreamDestroy(m->side);
+  }
+  if (m->side_fork) cudaEventDestroy(m->side_fork);
+  if (m->side_join) cudaEventDestroy(m->side_join);
   for (Depth& d : m->depth) {
     for (void* p : d.allocations) cudaFree(p);
     d.allocations.clear();
