@@ -380,6 +380,26 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = replica_time(float(np.mean(step_ms)), world)
 
+    # the other operators on the same workload (the paper's cost comparison)
+    def _time_op(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    nodal_ms = _time_op(lambda: H.hhg_apply_nodal(m.h, 0, u, y, H.HHG_F32, stream))
+    volface_ms = _time_op(lambda: H.hhg_apply_volface(m.h, 0, u, y, H.HHG_F32, stream))
+    operators = {"scaled_ms": ms, "nodal_ms": nodal_ms, "volface_ms": volface_ms,
+                 "nodal_over_scaled": nodal_ms / ms, "volface_over_scaled": volface_ms / ms}
+
     # end to end through the public API with host buffers
     uh = u.cpu().pin_memory()
     yh = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -458,7 +478,7 @@ def main():
                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
            "autotune": tune,
-           "clocks": clk.summary(), "wall_s_timed_region": wall, "solve": solve, "learned": learned, "mg_table": table}
+           "clocks": clk.summary(), "wall_s_timed_region": wall, "operators": operators, "solve": solve, "learned": learned, "mg_table": table}
     if rank == 0:
         print(json.dumps(out))
     m.close()

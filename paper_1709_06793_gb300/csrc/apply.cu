@@ -976,6 +976,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 3) nodal_staged_kern
 template <class T, class KT>
 static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk, void* y, cudaStream_t s) {
   const DepthDev& D = m.depth[depth].dev;
+  // interface rows on the side stream, concurrent with the volume kernel
+  const bool fork = D.n_items > 0 && D.n_bnodes > 0 && m.side;
+  if (fork) {
+    HHG_CUDA(cudaEventRecord(m.side_fork, s));
+    HHG_CUDA(cudaStreamWaitEvent(m.side, m.side_fork, 0));
+    nodal_boundary_kernel<T, KT><<<(D.n_bnodes + 127) / 128, 128, 0, m.side>>>(
+        D, static_cast<const T*>(u), static_cast<const KT*>(kk), static_cast<T*>(y));
+    HHG_CUDA(cudaGetLastError());
+    HHG_CUDA(cudaEventRecord(m.side_join, m.side));
+  }
   if (D.n_items > 0) {
     static int occ = 0;
     const int smem = 4 * Stage<T, KT>::warp_bytes;
@@ -989,7 +999,9 @@ static void nodal_typed(const Mesh& m, int depth, const void* u, const void* kk,
     nodal_staged_kernel<T, KT><<<blocks, 128, smem, s>>>(D, p);
     HHG_CUDA(cudaGetLastError());
   }
-  if (D.n_bnodes > 0) {
+  if (fork) {
+    HHG_CUDA(cudaStreamWaitEvent(s, m.side_join, 0));
+  } else if (D.n_bnodes > 0) {
     nodal_boundary_kernel<T, KT><<<(D.n_bnodes + 127) / 128, 128, 0, s>>>(
         D, static_cast<const T*>(u), static_cast<const KT*>(kk), static_cast<T*>(y));
     HHG_CUDA(cudaGetLastError());
@@ -1135,8 +1147,10 @@ void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpA
 // rows, summed over the copies and written to every copy, with the same
 // residual / Jacobi / diagonal epilogue as the scaled kernel.
 // ---------------------------------------------------------------------------
+// One warp per listed node: lanes take the (copy, micro tet) pairs, the warp
+// sums the row and its diagonal, the lanes write the copies.
 template <class T, class KT, int MODE>
-__global__ void volface_fixup_kernel(DepthDev D, OpPtrs p, int n_b) {
+__global__ void __launch_bounds__(128) volface_fixup_kernel(DepthDev D, OpPtrs p, int n_vf) {
   const T* elem;
   if constexpr (sizeof(T) == 8)
     elem = reinterpret_cast<const T*>(D.elem64);
@@ -1144,13 +1158,46 @@ __global__ void volface_fixup_kernel(DepthDev D, OpPtrs p, int n_b) {
     elem = reinterpret_cast<const T*>(D.elem32);
   const T* u = static_cast<const T*>(p.u);
   const KT* kk = static_cast<const KT*>(p.k);
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = warp; w < n_vf; w += nwarps) {
+    const int b = D.vf[w];
     const int lo = D.bstart[b], hi = D.bstart[b + 1];
-    if (D.bdir[b] || __popc((unsigned)D.bcopies[lo].mask) < 2) continue;
     T y = 0, dg = 0;
-    for (int q = lo; q < hi; ++q) {
-      const BCopy cp = D.bcopies[q];
-      y += nodal_partial<T, KT, true>(D.tets[cp.slot], elem + cp.slot * 96, cp.i, cp.j, cp.k, u, kk, true, &dg);
+    for (int pr = lane; pr < (hi - lo) * 24; pr += 32) {
+      const BCopy cp = D.bcopies[lo + pr / 24];
+      const TetDev td = D.tets[cp.slot];
+      const int N = td.N;
+      const NodalEntry& E = kNodal.e[pr % 24];
+      const long long x = td.base + node_offset(N, cp.i, cp.j, cp.k);
+      const T ux = u[x], kx = (T)ldk(kk, x);
+      const T* A = elem + cp.slot * 96 + E.sigma * 16 + E.v * 4;
+      bool ok = true;
+      T ksum = 0, inner = 0, asum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = cp.i + E.off[q][0], bb = cp.j + E.off[q][1], c = cp.k + E.off[q][2];
+        if (a < 0 || bb < 0 || c < 0 || a + bb + c > N) ok = false;
+        if (!ok) continue;
+        if (q == E.v) {
+          ksum += kx;
+        } else {
+          const long long idx = td.base + node_offset(N, a, bb, c);
+          ksum += (T)ldk(kk, idx);
+          inner = fma(A[q], u[idx] - ux, inner);
+          asum += A[q];
+        }
+      }
+      if (ok) {
+        y = fma(ksum, inner, y);
+        dg = fma(-ksum, asum, dg);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+      dg += __shfl_xor_sync(0xffffffffu, dg, o);
     }
     const long long i0 = D.bcopies[lo].idx;
     T val = y;
@@ -1161,17 +1208,17 @@ __global__ void volface_fixup_kernel(DepthDev D, OpPtrs p, int n_b) {
     } else if (MODE == OP_DIAG) {
       val = dg;
     }
-    for (int q = lo; q < hi; ++q) static_cast<T*>(p.out)[D.bcopies[q].idx] = val;
+    for (int q = lo + lane; q < hi; q += 32) static_cast<T*>(p.out)[D.bcopies[q].idx] = val;
   }
 }
 
 template <class T, class KT, int MODE>
 static void volface_typed(const Mesh& m, int depth, const OpArgs& a, const void* kptr, cudaStream_t s) {
   const DepthDev& D = m.depth[depth].dev;
-  const int n_b = a.nc_only ? D.n_bnodes_nc : D.n_bnodes;
-  if (n_b == 0) return;
+  const int n_vf = a.nc_only ? D.n_vf_nc : D.n_vf;
+  if (n_vf == 0) return;
   OpPtrs p{a.u, kptr, a.f, a.out, nullptr, nullptr, a.omega, 0, 0};
-  volface_fixup_kernel<T, KT, MODE><<<std::min((n_b + 127) / 128, 8 * m.num_sms), 128, 0, s>>>(D, p, n_b);
+  volface_fixup_kernel<T, KT, MODE><<<std::min((n_vf + 3) / 4, 16 * m.num_sms), 128, 0, s>>>(D, p, n_vf);
   HHG_CUDA(cudaGetLastError());
 }
 

@@ -87,6 +87,9 @@ struct DepthDev {
   int n_extra_nc;
   long long n_stored;
   long long n_stored_nc;
+  const int* vf;               // interface nodes on macro vertices/edges (not Dirichlet): indices into bstart
+  int n_vf;
+  int n_vf_nc;
   const int* fslot;            // slot of the same tet at depth-1 (-1 at depth 0)
   const unsigned char* mult;   // [slot][16] copies of a node of that face mask
 };
@@ -113,6 +116,8 @@ struct Depth {
   int n_rows = 0, n_rows_nc = 0;
   std::vector<long long> h_extra;
   int n_extra = 0, n_extra_nc = 0;
+  std::vector<int> h_vf;
+  int n_vf = 0, n_vf_nc = 0;
   std::vector<int> h_fslot;
   std::vector<unsigned char> h_mult;
   DepthDev dev{};

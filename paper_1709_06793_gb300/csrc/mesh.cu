@@ -485,6 +485,17 @@ static void build_depth(Mesh& m, int d) {
   }
   D.n_bnodes = (int)D.h_bdir.size();
   D.n_extra = (int)D.h_extra.size();
+  // interface nodes whose rows the "scale Vol+Face" operator takes from nodal
+  // integration: two or more face bits (macro edge or vertex), not Dirichlet
+  D.h_vf.clear();
+  D.n_vf_nc = 0;
+  for (int b = 0; b < D.n_bnodes; ++b) {
+    const int mask = D.h_bcopies[D.h_bstart[b]].mask;
+    if (D.h_bdir[b] || __builtin_popcount((unsigned)mask) < 2) continue;
+    D.h_vf.push_back(b);
+    if (b < D.n_bnodes_nc) D.n_vf_nc = (int)D.h_vf.size();
+  }
+  D.n_vf = (int)D.h_vf.size();
   // slot of the same tet one depth finer; copies per (slot, face mask)
   D.h_fslot.assign(ns, -1);
   if (d > 0)
@@ -542,6 +553,9 @@ static void upload_depth(Depth& D) {
   D.dev.bdir = upload(D, D.h_bdir);
   D.dev.n_bnodes = D.n_bnodes;
   D.dev.n_bnodes_nc = D.n_bnodes_nc;
+  D.dev.vf = upload(D, D.h_vf);
+  D.dev.n_vf = D.n_vf;
+  D.dev.n_vf_nc = D.n_vf_nc;
   D.dev.rows = upload(D, D.h_rows);
   D.dev.n_rows = D.n_rows;
   D.dev.n_rows_nc = D.n_rows_nc;
