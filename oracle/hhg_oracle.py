@@ -380,6 +380,66 @@ def volface_apply(lm, u, k):
 
 
 # ----------------------------------------------------------------------------
+# Tensor coefficient, M = 6 (eq. "integral" / eq. "meshdep" with M > 1;
+# Sec. 7.3): a(v, w) = sum_m int k_m (d_m . grad v)(d_m . grad w) with the
+# directions d = e1, e2, e3, e1-e2, e1-e3, e2-e3 and, for a symmetric K,
+# k_i = K_ii + sum_{j != i} K_ij and k_ij = -K_ij (non-negative when the
+# off-diagonal entries of K are <= 0, as in Sec. 7.3), so that
+# sum_m k_m d_m d_m^T = K.  Each a_m is scaled or nodally integrated like the
+# scalar form.
+# ----------------------------------------------------------------------------
+
+TENSOR_DIRS = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, -1, 0], [1, 0, -1], [0, 1, -1]], dtype=np.float64)
+
+
+def tensor_split(K6):
+    """K6 (n,6) = (K11, K22, K33, K12, K13, K23) -> the six k_m (n,6)."""
+    K6 = np.asarray(K6, dtype=np.float64)
+    K11, K22, K33, K12, K13, K23 = K6.T
+    return np.stack([K11 + K12 + K13, K22 + K12 + K23, K33 + K13 + K23, -K12, -K13, -K23], axis=1)
+
+
+def tensor_from_split(km):
+    """Inverse map: sum_m k_m d_m d_m^T as (n,3,3)."""
+    return np.einsum("nm,mi,mj->nij", np.asarray(km, dtype=np.float64), TENSOR_DIRS, TENSOR_DIRS)
+
+
+def p1_directional_stiffness(X, d):
+    """int_t (d . grad phi_a)(d . grad phi_b) = vol * (g_a . d)(g_b . d)."""
+    G, vol = p1_gradients(X)
+    gd = G @ np.asarray(d, dtype=np.float64)
+    return vol[:, None, None] * gd[:, :, None] * gd[:, None, :]
+
+
+def tensor_matrix(lm, km, kind="scaled"):
+    """Full n x n matrix of sum_m a_m^h (kind "scaled", eq. "discrete" per m)
+    or of the nodal-integration form (kind "nodal", mean k_m per micro tet);
+    km: (n,6) nodal values of the k_m."""
+    km = np.asarray(km, dtype=np.float64)
+    R, C, D = [], [], []
+    for t in range(len(lm.macro.T)):
+        ids = lm.micro[t]
+        X = lm.coords[ids]
+        M = np.zeros((len(ids), 4, 4))
+        for m in range(6):
+            A = p1_directional_stiffness(X, TENSOR_DIRS[m])
+            kv = km[ids, m]
+            M += scaled_element(A, kv) if kind == "scaled" else nodal_element(A, kv)
+        R.append(np.repeat(ids, 4, axis=1).reshape(-1))
+        C.append(np.tile(ids, (1, 4)).reshape(-1))
+        D.append(M.reshape(-1))
+    return sp.csr_matrix((np.concatenate(D), (np.concatenate(R), np.concatenate(C))), shape=(lm.n, lm.n))
+
+
+def tensor_apply(lm, u, km, kind="scaled"):
+    """y = A u on the unknowns (Dirichlet entries of u taken as 0, those of y 0)."""
+    u = np.where(lm.dirichlet, 0.0, np.asarray(u, dtype=np.float64))
+    y = tensor_matrix(lm, km, kind) @ u
+    y[lm.dirichlet] = 0.0
+    return y
+
+
+# ----------------------------------------------------------------------------
 # One row at a time (for sampled checks at sizes too large to enumerate)
 # ----------------------------------------------------------------------------
 
@@ -466,7 +526,7 @@ class Hierarchy:
     coarse nodes equals injecting the fine nodal values).  All matrices act on
     unknowns only."""
 
-    def __init__(self, V, T, finest, coarsest, k_func=None, k_fine=None, kind="scaled",
+    def __init__(self, V, T, finest, coarsest, k_func=None, k_fine=None, kind="scaled", K_func=None,
                  smoother="jacobi", omega=2.0 / 3.0, cheb_degree=2, cheb_lo=0.3, cheb_hi=1.1,
                  power_its=15):
         self.macro = MacroMesh(V, T)
@@ -476,6 +536,12 @@ class Hierarchy:
         self.A, self.D, self.P, self.k = {}, {}, {}, {}
         for l in self.levels:
             lm = self.mesh[l]
+            if K_func is not None:  # tensor coefficient (M = 6), scaled form
+                kl = tensor_split(K_func(lm.coords))
+                self.k[l] = kl
+                self.A[l] = tensor_matrix(lm, kl, "scaled")[lm.unknowns][:, lm.unknowns].tocsr()
+                self.D[l] = self.A[l].diagonal()
+                continue
             if k_fine is not None:
                 kl = self._inject(k_fine, l)
             else:

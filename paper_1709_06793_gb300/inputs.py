@@ -221,6 +221,48 @@ def f_sine_cosine_k(m):
     return f
 
 
+def K_tensor(x):
+    """The permeability tensor of the paper's 3D tensor test (Sec. 7.3), as
+    (n,6) = (K11, K22, K33, K12, K13, K23); its off-diagonal entries are <= 0."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[:, 0] ** 2, x[:, 1] ** 2, x[:, 2] ** 2
+    return np.stack([X + 2 * Y + 3 * Z + 1, 2 * X + 3 * Y + Z + 1, 3 * X + Y + 2 * Z + 1, -Y, -Z, -X], axis=1)
+
+
+def f_sine_tensor(x):
+    """f = -div(K grad u) for K = K_tensor and u = u_sine."""
+    x = np.asarray(x, dtype=np.float64)
+    p = np.pi
+    sx, sy, sz = np.sin(p * x[:, 0]), np.sin(p * x[:, 1]), np.sin(p * x[:, 2])
+    cx, cy, cz = np.cos(p * x[:, 0]), np.cos(p * x[:, 1]), np.cos(p * x[:, 2])
+    g = np.stack([p * cx * sy * sz, p * sx * cy * sz, p * sx * sy * cz], axis=1)  # grad u
+    H = np.empty((len(x), 3, 3))  # Hessian of u
+    H[:, 0, 0] = H[:, 1, 1] = H[:, 2, 2] = -p * p * sx * sy * sz
+    H[:, 0, 1] = H[:, 1, 0] = p * p * cx * cy * sz
+    H[:, 0, 2] = H[:, 2, 0] = p * p * cx * sy * cz
+    H[:, 1, 2] = H[:, 2, 1] = p * p * sx * cy * cz
+    K6 = K_tensor(x)
+    K = np.empty((len(x), 3, 3))
+    K[:, 0, 0], K[:, 1, 1], K[:, 2, 2] = K6[:, 0], K6[:, 1], K6[:, 2]
+    K[:, 0, 1] = K[:, 1, 0] = K6[:, 3]
+    K[:, 0, 2] = K[:, 2, 0] = K6[:, 4]
+    K[:, 1, 2] = K[:, 2, 1] = K6[:, 5]
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    # div of K's columns: d/dx_j K_ij summed over j, for each row i
+    divK = np.empty((len(x), 3))
+    dK11 = (2 * X, 4 * Y, 6 * Z)
+    dK22 = (4 * X, 6 * Y, 2 * Z)
+    dK33 = (6 * X, 2 * Y, 4 * Z)
+    dK12 = (0 * X, -2 * Y, 0 * Z)
+    dK13 = (0 * X, 0 * Y, -2 * Z)
+    dK23 = (-2 * X, 0 * Y, 0 * Z)
+    # (div K)_j = sum_i d/dx_i K_ij
+    divK[:, 0] = dK11[0] + dK12[1] + dK13[2]
+    divK[:, 1] = dK12[0] + dK22[1] + dK23[2]
+    divK[:, 2] = dK13[0] + dK23[1] + dK33[2]
+    return -(np.einsum("nj,nj->n", divK, g) + np.einsum("nij,nij->n", K, H))
+
+
 def k_large(x):
     """1 + 0.5 sin(4 pi x) cos(4 pi y) sin(4 pi z)."""
     x = np.asarray(x, dtype=np.float64)
