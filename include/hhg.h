@@ -85,7 +85,8 @@ typedef enum {
 typedef enum {
     HHG_OP_SCALED = 0,         /* stencil scaling on every row (eq. "discrete") */
     HHG_OP_VOLFACE = 1,        /* "scale Vol+Face": nodal rows on macro vertices/edges (eq. "modst") */
-    HHG_OP_NODAL = 2           /* nodal integration on every row (eq. "standardfe") */
+    HHG_OP_NODAL = 2,          /* nodal integration on every row (eq. "standardfe") */
+    HHG_OP_TENSOR = 3          /* stencil scaling of the tensor coefficient (M = 6, hhg_set_tensor_coefficient) */
 } hhg_operator;
 
 typedef struct {
@@ -98,7 +99,7 @@ typedef struct {
     double inner_rtol;   /* MIXED: relative residual reduction of each inner solve (default 1e-4) */
     int max_outer;       /* MIXED: max refinement steps (default 20) */
     int use_graph;       /* capture each CG iteration in a CUDA graph (1) or launch eagerly (0) */
-    int op;              /* hhg_operator; HHG_OP_VOLFACE and HHG_OP_NODAL need mode HHG_SOLVE_MG
+    int op;              /* hhg_operator; HHG_OP_VOLFACE, HHG_OP_NODAL, HHG_OP_TENSOR need mode HHG_SOLVE_MG
                             and Jacobi smoothing (coarsest level: dense LU of that operator) */
 } hhg_solve_params;
 
@@ -224,6 +225,22 @@ int hhg_autotune(hhg_mesh mesh, int dtype, const char* cache_path, int* kseg, in
  * "repro"); not symmetric (the asymmetry is O(h^2)).  Arguments, layout and
  * errors as hhg_apply_scaled; u_dev and y_dev must not overlap. */
 int hhg_apply_volface(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
+
+/* Tensor coefficient K (Sec. 7.3; eq. "integral" and eq. "meshdep" with
+ * M = 6).  K6_dev: FP64 device array of 6 x n_stored(depth 0), component
+ * major: K11, K22, K33, K12, K13, K23 at every stored node.  The library
+ * splits K = sum_m k_m d_m d_m^T along d = e1, e2, e3, e1-e2, e1-e3, e2-e3
+ * (k_i = K_ii + sum_{j != i} K_ij, k_ij = -K_ij; all k_m >= 0 when the
+ * off-diagonal entries of K are <= 0, as in the paper's test), injects the
+ * k_m to every depth and builds the six terms' reference stencils on first
+ * use.  Independent of hhg_set_coefficient. */
+int hhg_set_tensor_coefficient(hhg_mesh mesh, const void* K6_dev, void* stream);
+
+/* y = A_K u: every row sum_m sum_d c^m_d (k_m(x) + k_m(x+w_d)) (u_{x+w_d} - u_x)
+ * with c^m the (1/2) reference stencil of (d_m . grad)(d_m . grad).  dtype
+ * HHG_F64 or HHG_F32; u_dev and y_dev must not overlap; HHG_ERR_STATE without
+ * a tensor coefficient. */
+int hhg_apply_tensor(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
 
 /* r = f - A_s(k) u at `depth` (the residual of the paper's benchmark, Sec. 7.4). */
 int hhg_residual(hhg_mesh mesh, int depth, const void* f_dev, const void* u_dev, void* r_dev,

@@ -11,6 +11,8 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 size_t elem_size(int dtype);
 void set_coefficient(Mesh& m, const double* k, cudaStream_t s);
+void set_tensor_coefficient(Mesh& m, const double* K6, cudaStream_t s);
+void* workspace(Mesh& m, int depth, int prec, int w);
 void apply_scaled(Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 void residual(Mesh& m, int depth, int dtype, const void* f, const void* u, void* r, bool nc_only, cudaStream_t s);
 void smooth(Mesh& m, int depth, int dtype, int kind, int sweeps, double omega, const void* f, void* u, bool nc_only,
@@ -192,6 +194,30 @@ int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, in
     need_vec(y_dev, "y_dev");
     if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
     launch_nodal_apply(m, depth, dtype, u_dev, y_dev, (cudaStream_t)stream);
+  });
+}
+
+int hhg_set_tensor_coefficient(hhg_mesh mesh, const void* K6_dev, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_ptr(K6_dev, "K6_dev");
+    set_tensor_coefficient(m, static_cast<const double*>(K6_dev), (cudaStream_t)stream);
+  });
+}
+
+int hhg_apply_tensor(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream) {
+  return guarded([&] {
+    Mesh& m = need(mesh);
+    need_depth(m, depth);
+    if (dtype != HHG_F64 && dtype != HHG_F32) throw Error{HHG_ERR_ARG, "hhg_apply_tensor: dtype HHG_F64 or HHG_F32"};
+    if (!m.tensor_set) throw Error{HHG_ERR_STATE, "hhg_set_tensor_coefficient must be called first"};
+    need_vec(u_dev, "u_dev");
+    need_vec(y_dev, "y_dev");
+    if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
+    const int pr = dtype == HHG_F64 ? 0 : 1;
+    OpArgs a{u_dev, nullptr, y_dev, nullptr, nullptr, 0, 0, 0, 0};
+    launch_tensor_op(m, depth, dtype, OP_APPLY, a, workspace(m, depth, pr, 12), workspace(m, depth, pr, 13),
+                     (cudaStream_t)stream);
   });
 }
 

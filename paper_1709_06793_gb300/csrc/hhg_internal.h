@@ -125,6 +125,12 @@ struct Depth {
   std::vector<void*> allocations;
   // coefficient copies at this depth
   double* k16d = nullptr;  // bfloat16-rounded k held in double (outer residual of the bf16 solve)
+  // tensor coefficient (six terms, component-major: 6 x n_stored) and the
+  // six terms' reference stencils [slot][6][16][14] (set on first use)
+  double* km64 = nullptr;
+  float* km32 = nullptr;
+  const double* tsten64 = nullptr;
+  const float* tsten32 = nullptr;
   double* k64 = nullptr;
   float* k32 = nullptr;
   __nv_bfloat16* k16 = nullptr;
@@ -132,7 +138,8 @@ struct Depth {
   // slots: 0 F (depth>0) / CG r (depth 0), 1 U / CG z, 2 V-cycle residual,
   // 3 CG p, 4 smoother ping-pong, 5-6 Chebyshev updates, 7 CG q, 8 inner solution
   // 9 inner solution, 10 operator scratch (nodal modes), 11 spare
-  void* ws[2][12] = {{nullptr}};
+  // 12-13 tensor-operator partial rows and diagonals
+  void* ws[2][14] = {{nullptr}};
   void* ndinv[4] = {nullptr, nullptr, nullptr, nullptr};  // nodal operator 1/diag per dtype (0 on Dirichlet)
   int* cslot_map = nullptr;  // slot at depth+1 of each slot (prolongation)
   double lam = 0.0;  // lambda_max of D^-1 A (FP64, 0 = not yet estimated)
@@ -173,9 +180,10 @@ struct Mesh {
   // operator of the multigrid internals (V-cycle, smoothers, residuals, coarse
   // solve): 0 scaled, 1 "scale Vol+Face", 2 nodal integration; set by the
   // multigrid solve for its duration, 0 otherwise
-  int opk = 0;
-  bool cinv_ready[3][4] = {};         // per operator and dtype
-  double* d_cinv[3][4] = {};          // dense coarse inverses (packed)
+  int opk = 0;                        // 3: scaled tensor coefficient (M = 6)
+  bool tensor_set = false;
+  bool cinv_ready[4][4] = {};         // per operator and dtype
+  double* d_cinv[4][4] = {};          // dense coarse inverses (packed)
   std::vector<long long> cinv_off;  // per component offset into d_cinv
   // scratch
   double* d_red = nullptr;        // reduction partials
@@ -264,6 +272,10 @@ void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void
 void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 // nodal-integration operator in the modes above (dinv: 1/diag, 0 on Dirichlet nodes; tmp: a scratch vector)
 void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s);
+// scaled operator of the tensor coefficient (M = 6) in the modes above (py, pd: scratch vectors)
+void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, void* py, void* pd,
+                      cudaStream_t s);
+void ensure_tensor_stencils(Mesh& m);
 void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, const void* dinv, void* tmp,
                      cudaStream_t s);
 void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);

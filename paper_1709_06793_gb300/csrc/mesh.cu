@@ -84,8 +84,10 @@ static std::vector<Micro> micro_at(int N, int i, int j, int k) {
   return out;
 }
 
-// P1 stiffness matrix of the tetrahedron X[4][3]: vol * grad phi_a . grad phi_b.
-static void p1_stiffness(const double X[4][3], double A[4][4]) {
+// P1 stiffness matrix of the tetrahedron X[4][3]: vol * grad phi_a . grad phi_b;
+// with a direction d: vol * (d . grad phi_a)(d . grad phi_b) (one term of the
+// tensor coefficient's split).
+static void p1_stiffness(const double X[4][3], double A[4][4], const double* d = nullptr) {
   double J[3][3];
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) J[r][c] = X[c + 1][r] - X[0][r];  // columns = edge vectors
@@ -111,6 +113,13 @@ static void p1_stiffness(const double X[4][3], double A[4][4]) {
     G[0][c] = -(G[1][c] + G[2][c] + G[3][c]);
   }
   const double vol = std::fabs(det) / 6.0;
+  if (d) {
+    double gd[4];
+    for (int a = 0; a < 4; ++a) gd[a] = G[a][0] * d[0] + G[a][1] * d[1] + G[a][2] * d[2];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) A[a][b] = vol * gd[a] * gd[b];
+    return;
+  }
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) A[a][b] = vol * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
 }
@@ -172,6 +181,49 @@ void stencils_for(const Mesh& m, int tet, int level, double* out) {
         out[mask * kNDir + d] += 0.5 * A[mt.v][q];
       }
     }
+  }
+}
+
+// Reference stencils of the six terms of a tensor coefficient (directions e1,
+// e2, e3, e1-e2, e1-e3, e2-e3): out[m][mask][d] = (1/2) sum over the micro
+// tets at the primitive's node of vol (d_m . grad phi_x)(d_m . grad phi_y).
+void tensor_stencils_for(const Mesh& m, int tet, int level, double* out) {
+  static const double dirs[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, -1, 0}, {1, 0, -1}, {0, 1, -1}};
+  const int N = 1 << level;
+  std::fill(out, out + 6 * 16 * kNDir, 0.0);
+  for (int mask = 0; mask < 16; ++mask) {
+    int rep[3];
+    if (!representative(N, mask, rep)) continue;
+    for (const Micro& mt : micro_at(N, rep[0], rep[1], rep[2])) {
+      double X[4][3];
+      for (int q = 0; q < 4; ++q) index_to_phys(m, tet, N, mt.ijk[q], X[q]);
+      for (int t = 0; t < 6; ++t) {
+        double A[4][4];
+        p1_stiffness(X, A, dirs[t]);
+        for (int q = 0; q < 4; ++q) {
+          if (q == mt.v) continue;
+          const int d = dir_index(mt.ijk[q][0] - rep[0], mt.ijk[q][1] - rep[1], mt.ijk[q][2] - rep[2]);
+          HHG_REQUIRE(d >= 0, "internal: micro-tet edge not in the 15-point pattern");
+          out[(t * 16 + mask) * kNDir + d] += 0.5 * A[mt.v][q];
+        }
+      }
+    }
+  }
+}
+
+// Device copies of the tensor stencils of every depth (built on first use).
+void ensure_tensor_stencils(Mesh& m) {
+  for (Depth& D : m.depth) {
+    if (D.tsten64) continue;
+    const int ns = (int)D.slot_tet.size();
+    std::vector<double> h((size_t)std::max(ns, 1) * 6 * 16 * kNDir, 0.0);
+    for (int s = 0; s < ns; ++s) {
+      const int t = D.slot_tet[s];
+      tensor_stencils_for(m, t, D.tet_level[t], &h[(size_t)s * 6 * 16 * kNDir]);
+    }
+    std::vector<float> h32(h.begin(), h.end());
+    D.tsten64 = upload(D, h);
+    D.tsten32 = upload(D, h32);
   }
 }
 

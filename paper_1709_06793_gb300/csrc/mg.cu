@@ -67,6 +67,49 @@ __global__ void inject_kernel(DepthDev C, DepthDev F, const V* __restrict__ fine
   }
 }
 
+// k_m of the six-term split of a symmetric tensor (directions e1, e2, e3,
+// e1-e2, e1-e3, e2-e3): k_i = K_ii + sum_{j != i} K_ij, k_ij = -K_ij
+__global__ void tensor_split_kernel(const double* __restrict__ K6, long long n, double* __restrict__ km64,
+                                    float* __restrict__ km32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double K11 = K6[i], K22 = K6[n + i], K33 = K6[2 * n + i];
+    const double K12 = K6[3 * n + i], K13 = K6[4 * n + i], K23 = K6[5 * n + i];
+    const double v[6] = {K11 + K12 + K13, K22 + K12 + K23, K33 + K13 + K23, -K12, -K13, -K23};
+    for (int m = 0; m < 6; ++m) {
+      km64[m * n + i] = v[m];
+      km32[m * n + i] = (float)v[m];
+    }
+  }
+}
+
+void set_tensor_coefficient(Mesh& m, const double* K6, cudaStream_t s) {
+  drop_graphs(m);
+  ensure_tensor_stencils(m);
+  for (int d = 0; d < m.ndepth; ++d) {
+    Depth& D = m.depth[d];
+    const size_t n = std::max<long long>(D.n_stored, 1);
+    if (!D.km64) {
+      D.km64 = static_cast<double*>(dalloc(D, 6 * n * 8));
+      D.km32 = static_cast<float*>(dalloc(D, 6 * n * 4));
+    }
+  }
+  Depth& D0 = m.depth[0];
+  tensor_split_kernel<<<grid_for(D0.n_stored, 256, 4096), 256, 0, s>>>(K6, D0.n_stored, D0.km64, D0.km32);
+  HHG_CUDA(cudaGetLastError());
+  for (int d = 1; d < m.ndepth; ++d) {
+    Depth& C = m.depth[d];
+    Depth& F = m.depth[d - 1];
+    const int g = grid_for((long long)C.n_rows * 32, 256, 4096);
+    for (int t = 0; t < 6; ++t) {
+      inject_kernel<double><<<g, 256, 0, s>>>(C.dev, F.dev, F.km64 + t * F.n_stored, C.km64 + t * C.n_stored);
+      inject_kernel<float><<<g, 256, 0, s>>>(C.dev, F.dev, F.km32 + t * F.n_stored, C.km32 + t * C.n_stored);
+    }
+    HHG_CUDA(cudaGetLastError());
+  }
+  m.tensor_set = true;
+  for (int t = 0; t < 4; ++t) m.cinv_ready[3][t] = false;
+}
+
 void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
   drop_graphs(m);
   learned_invalidate(m);
@@ -95,7 +138,7 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
     HHG_CUDA(cudaGetLastError());
   }
   m.coef_set = true;
-  for (int o = 0; o < 3; ++o)
+  for (int o = 0; o < 4; ++o)
     for (int t = 0; t < 4; ++t) m.cinv_ready[o][t] = false;
   for (Depth& D : m.depth)
     for (int t = 0; t < 4; ++t)
@@ -589,7 +632,10 @@ const void* nodal_dinv(Mesh& m, int depth, int dtype, cudaStream_t s) {
 static void op(Mesh& m, int depth, int dtype, OpMode mode, const void* u, const void* f, void* out, const void* din,
                void* dout, double omega, double ca, double cb, bool nc_only, cudaStream_t s) {
   OpArgs a{u, f, out, din, dout, omega, ca, cb, nc_only ? 1 : 0};
-  if (m.opk == 1)
+  if (m.opk == 3)
+    launch_tensor_op(m, depth, dtype, mode, a, workspace(m, depth, prec_of(dtype), 12),
+                     workspace(m, depth, prec_of(dtype), 13), s);
+  else if (m.opk == 1)
     launch_volface_op(m, depth, dtype, mode, a, s);
   else if (m.opk == 2)
     launch_nodal_op(m, depth, dtype, mode, a, nodal_dinv(m, depth, dtype, s), workspace(m, depth, prec_of(dtype), 10),

@@ -261,8 +261,9 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
   if (p.maxit <= 0) p.maxit = 200;
   HHG_REQUIRE(p.tol > 0, "tol must be positive");
   HHG_REQUIRE(p.mode >= 0 && p.mode <= 3, "unknown solve mode");
-  HHG_REQUIRE(p.op >= 0 && p.op <= 2, "unknown operator");
-  HHG_REQUIRE(p.op == 0 || p.mode == HHG_SOLVE_MG, "the Vol+Face and nodal operators are solved with HHG_SOLVE_MG");
+  HHG_REQUIRE(p.op >= 0 && p.op <= 3, "unknown operator");
+  HHG_REQUIRE(p.op != 3 || m.tensor_set, "hhg_set_tensor_coefficient must be called first");
+  HHG_REQUIRE(p.op == 0 || p.mode == HHG_SOLVE_MG, "the Vol+Face, nodal and tensor operators are solved with HHG_SOLVE_MG");
   if (p.mode == HHG_SOLVE_MG) return solve_mg(m, p, f, u, st, s);
   const auto t0 = std::chrono::steady_clock::now();
   const long long n = m.depth[0].n_stored;

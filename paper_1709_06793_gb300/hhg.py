@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhhg.so")
 HHG_F64, HHG_F32, HHG_F32_KBF16 = 0, 1, 2
 HHG_SMOOTH_JACOBI, HHG_SMOOTH_CHEBYSHEV, HHG_SMOOTH_LEARNED = 0, 1, 2
 HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16, HHG_SOLVE_MG = 0, 1, 2, 3
-HHG_OP_SCALED, HHG_OP_VOLFACE, HHG_OP_NODAL = 0, 1, 2
+HHG_OP_SCALED, HHG_OP_VOLFACE, HHG_OP_NODAL, HHG_OP_TENSOR = 0, 1, 2, 3
 STATUS = {0: "HHG_OK", -1: "HHG_ERR_ARG", -2: "HHG_ERR_CUDA", -3: "HHG_ERR_NOMEM",
           -4: "HHG_ERR_NOT_CONVERGED", -5: "HHG_ERR_TIMEOUT", -6: "HHG_ERR_STATE"}
 
@@ -74,6 +74,8 @@ def _load():
         "hhg_apply_scaled": [P, I, P, P, I, P],
         "hhg_apply_nodal": [P, I, P, P, I, P],
         "hhg_apply_volface": [P, I, P, P, I, P],
+        "hhg_set_tensor_coefficient": [P, P, P],
+        "hhg_apply_tensor": [P, I, P, P, I, P],
         "hhg_residual": [P, I, P, P, P, I, P],
         "hhg_apply_mass": [P, I, P, P, I, P],
         "hhg_autotune": [P, I, C.c_char_p, C.POINTER(I), C.POINTER(I), C.POINTER(D), P],
@@ -202,6 +204,15 @@ def hhg_apply_nodal(mesh, depth, u, y, dtype, stream=None):
 
 def hhg_apply_volface(mesh, depth, u, y, dtype, stream=None):
     _check(_lib.hhg_apply_volface(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
+
+
+def hhg_set_tensor_coefficient(mesh, K6, stream=None):
+    """K6: FP64 device tensor of shape (6, n_stored) = (K11, K22, K33, K12, K13, K23)."""
+    _check(_lib.hhg_set_tensor_coefficient(mesh, _ptr(K6), _stream(stream)))
+
+
+def hhg_apply_tensor(mesh, depth, u, y, dtype, stream=None):
+    _check(_lib.hhg_apply_tensor(mesh, depth, _ptr(u), _ptr(y), dtype, _stream(stream)))
 
 
 def hhg_apply_mass(mesh, depth, u, y, dtype, stream=None):

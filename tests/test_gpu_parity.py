@@ -462,3 +462,60 @@ def test_mg_solver_rejects_operator_outside_mg_mode(H):
     with pytest.raises(H.HHGError, match="HHG_SOLVE_MG"):
         H.hhg_solve(c.m.h, c.dev(c.rand_or, 0), u, mode=H.HHG_SOLVE_FP64, op=H.HHG_OP_VOLFACE)
     c.m.close()
+
+
+def _tensor_case(H, name):
+    mesh, level, coarsest, kf = MESHES[name]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    K6 = np.ascontiguousarray(I.K_tensor(c.xyz).T)  # (6, n_stored)
+    H.hhg_set_tensor_coefficient(c.m.h, torch.tensor(K6, device="cuda"))
+    return c, (V, T, level, coarsest)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3"])
+def test_tensor_apply_parity(H, name, dtype):
+    """Scaled operator of the tensor coefficient (M = 6) against the oracle's
+    element loop over the six terms; FP32 on FP32-rounded inputs."""
+    c, _ = _tensor_case(H, name)
+    km = O.tensor_split(I.K_tensor(c.lm.coords))
+    u = c.rand_or
+    if dtype == H.HHG_F32:
+        km, u = _f32(km), _f32(u)
+    ud = c.dev(u, dtype)
+    y = torch.empty_like(ud)
+    H.hhg_apply_tensor(c.m.h, 0, ud, y, dtype)
+    torch.cuda.synchronize()
+    got = c.back(y)
+    want = O.tensor_apply(c.lm, u, km, "scaled")
+    tol = 1e-12 if dtype == H.HHG_F64 else 1e-6
+    assert _rel(got, want) <= tol, _rel(got, want)
+    assert np.all(got[c.dir] == 0)
+    c.m.close()
+
+
+@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3"])
+def test_tensor_mg_solver_parity(H, name):
+    c, (V, T, level, coarsest) = _tensor_case(H, name)
+    Ho = O.Hierarchy(V, T, level, coarsest, K_func=I.K_tensor)
+    fu = c.rand_or[c.lm.unknowns]
+    for its in (3, 10):
+        u = torch.zeros(c.n, device="cuda", dtype=torch.float64)
+        st = H.hhg_solve(c.m.h, c.dev(c.rand_or, 0), u, tol=1e-30, maxit=its, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3,
+                         op=H.HHG_OP_TENSOR, raise_on_fail=False)
+        x, hist = Ho.mg_solve(fu, its)
+        assert _rel(c.back(u)[c.lm.unknowns], x) <= 1e-10
+        if its == 10:
+            assert abs(st["rho"] - O.mg_rate(hist)) <= 1e-6 * O.mg_rate(hist)
+    c.m.close()
+
+
+def test_tensor_operator_needs_its_coefficient(H):
+    mesh, level, coarsest, kf = MESHES["kuhn_cube_l4"]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    ud = c.dev(c.rand_or, 0)
+    with pytest.raises(H.HHGError, match="tensor"):
+        H.hhg_apply_tensor(c.m.h, 0, ud, torch.empty_like(ud), H.HHG_F64)
+    c.m.close()
