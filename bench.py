@@ -303,6 +303,65 @@ def paper_table(H, I, torch, m_big=None, levels=TABLE_LEVELS):
             "rows": rows}
 
 
+TENSOR_LEVELS = (3, 4, 5, 6, 7)  # the paper's L = 1 .. 5 on the 12-tet cube
+
+
+def tensor_table(H, I, torch, flush, levels=TENSOR_LEVELS):
+    """Shape of the paper's tensor test (Sec. 7.3, Tab. "divK4"): the 12-tet
+    cube, its permeability tensor K, multigrid V(3,3) (FP64) until the
+    residual drops by 1e-9; discrete L2 error of u* = sin(pi x) sin(pi y)
+    sin(pi z), eoc, rho, time to solution.  Plus the FP32 tensor apply on the
+    finest level against its HBM roofline (u, six k_m, y: 32 B per node)."""
+    V, T = I.cube12()
+    rows, prev = [], None
+    apply = None
+    for level in levels:
+        m = H.Mesh(V, T, level, 1)
+        off, lev, n = m.layout(0)
+        xyz = m.coords(0)
+        H.hhg_set_tensor_coefficient(m.h, torch.tensor(np.ascontiguousarray(I.K_tensor(xyz).T), device="cuda"))
+        fi = torch.tensor(I.f_sine_tensor(xyz), device="cuda")
+        f = torch.empty_like(fi)
+        H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
+        w = torch.empty_like(fi)
+        H.hhg_apply_mass(m.h, 0, torch.ones_like(fi), w, H.HHG_F64)
+        u = torch.zeros(n, device="cuda", dtype=torch.float64)
+        kw = dict(tol=1e-9, maxit=60, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3, op=H.HHG_OP_TENSOR, raise_on_fail=False)
+        H.hhg_solve(m.h, f, u, **kw)
+        u.zero_()
+        torch.cuda.synchronize()
+        st = H.hhg_solve(m.h, f, u, **kw)
+        e = u - torch.tensor(I.u_sine(xyz), device="cuda")
+        err = math.sqrt(max(H.hhg_dot(m.h, 0, w * e, e, H.HHG_F64), 0.0))
+        rows.append({"level": level, "L": level - 2, "stored_nodes": n, "error": err, "eoc": math.log2(prev / err) if prev else None, "rho": st["rho"],
+                     "cycles": st["iterations"], "tts_ms": st["time_ms"]})
+        prev = err
+        if level == levels[-1]:
+            x = torch.rand(n, device="cuda", dtype=torch.float32)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
+            ts = []
+            for i in range(10):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = float(np.mean(ts))
+            peaks, src = _peaks()
+            ach = 32 * n / (ms * 1e-3) / 1e9
+            apply = {"level": level, "stored_nodes": n, "ms": ms,
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_node": 32}}
+        m.close()
+    return {"workload": "unit cube, 12 macro-tets, K = the paper's tensor (Sec. 7.3), u* = sin(pi x) sin(pi y) "
+                        "sin(pi z); V(3,3) (damped Jacobi) to a 1e-9 residual reduction, FP64",
+            "rows": rows, "apply_fp32": apply}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +372,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--no-table", action="store_true", help="skip the multigrid table (nodal / Vol+Face / scaled)")
+    ap.add_argument("--no-table", action="store_true", help="skip the multigrid tables (scalar and tensor)")
     ap.add_argument("--only-learned", action="store_true",
                     help="run only the learned-smoother section (C4) and print its JSON")
     ap.add_argument("--tune-cache", action="store_true", help="reuse/append autotuner results in _build_tune.txt")
@@ -458,9 +517,10 @@ def main():
                            "rhs M I_h f; FP64 outer residual in every mode")
         solve["speedup_mixed_vs_fp64"] = solve["fp64"]["ms"] / solve["mixed_fp32_fp64refine"]["ms"]
 
-    table = None
+    table = tensor = None
     if not args.no_table:
         table = paper_table(H, I, torch, m_big=m)
+        tensor = tensor_table(H, I, torch, flush)
 
     learned = None
     if not args.no_learned:
@@ -478,7 +538,7 @@ def main():
                       "l2": "flushed before every step (512 MiB write, outside the step events)"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
            "autotune": tune,
-           "clocks": clk.summary(), "wall_s_timed_region": wall, "operators": operators, "solve": solve, "learned": learned, "mg_table": table}
+           "clocks": clk.summary(), "wall_s_timed_region": wall, "operators": operators, "solve": solve, "learned": learned, "mg_table": table, "tensor_table": tensor}
     if rank == 0:
         print(json.dumps(out))
     m.close()

@@ -368,8 +368,8 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
   int status = HHG_OK;
   const int rc = guarded([&] {
     Mesh& m = need(mesh);
-    need_coef(m);
     need_ptr(p, "params");
+    if (p->op != HHG_OP_TENSOR) need_coef(m);
     need_vec(f_dev, "f_dev");
     need_vec(u_dev, "u_dev");
     if (p->smoother < 0 || p->smoother > 2) throw Error{HHG_ERR_ARG, "unknown smoother"};

@@ -69,7 +69,7 @@ void drop_graphs(Mesh& m) {
 // Allocate every buffer and estimate every quantity a V-cycle / CG needs, so
 // that afterwards the iteration only enqueues kernels (capturable).
 void prepare(Mesh& m, int dtype, int smoother, cudaStream_t s) {
-  HHG_REQUIRE(m.coef_set, "hhg_set_coefficient must be called first");
+  if (!m.coef_set && m.opk != 3) throw Error{HHG_ERR_STATE, "hhg_set_coefficient must be called first"};
   HHG_REQUIRE(m.opk == 0 || smoother == HHG_SMOOTH_JACOBI,
               "the Vol+Face and nodal operators are smoothed with damped Jacobi");
   const int pr = prec_of(dtype);

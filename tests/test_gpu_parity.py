@@ -519,3 +519,16 @@ def test_tensor_operator_needs_its_coefficient(H):
     with pytest.raises(H.HHGError, match="tensor"):
         H.hhg_apply_tensor(c.m.h, 0, ud, torch.empty_like(ud), H.HHG_F64)
     c.m.close()
+
+
+def test_tensor_mg_solve_needs_no_scalar_coefficient(H):
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, 4, 2)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_tensor_coefficient(m.h, torch.tensor(np.ascontiguousarray(I.K_tensor(xyz).T), device="cuda"))
+    f = torch.tensor(np.where(np.any((xyz <= 0) | (xyz >= 1), axis=1), 0.0, 1.0), device="cuda")
+    u = torch.zeros(n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(m.h, f, u, tol=1e-9, maxit=60, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3, op=H.HHG_OP_TENSOR)
+    assert st["rel_residual"] <= 1e-9 and 0 < st["rho"] < 0.5
+    m.close()
