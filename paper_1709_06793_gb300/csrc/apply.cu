@@ -1264,6 +1264,18 @@ __device__ __forceinline__ T tensor_finish(T y, T dg, T ux, long long idx, const
   return y;
 }
 
+// the six k_m of a node (node-major, 8- or 16-byte aligned: three vector loads)
+__device__ __forceinline__ void load6(const float* p, float (&v)[6]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  const float2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+__device__ __forceinline__ void load6(const double* p, double (&v)[6]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) tensor_rows_kernel(DepthDev D, const T* __restrict__ tsten,
                                                           const T* __restrict__ km, long long nst, OpPtrs p,
@@ -1282,8 +1294,7 @@ __global__ void __launch_bounds__(256) tensor_rows_kernel(DepthDev D, const T* _
       const long long x = td.base + node_offset(N, i, j, k);
       const T ux = u[x];
       T kx[6];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) kx[m] = km[m * nst + x];
+      load6(km + 6 * x, kx);
       T y = 0, dg = 0;
 #pragma unroll
       for (int d = 0; d < kNDir; ++d) {
@@ -1293,9 +1304,11 @@ __global__ void __launch_bounds__(256) tensor_rows_kernel(DepthDev D, const T* _
         if (a < 0 || b < 0 || c < 0 || a + b + c > N) continue;
         const long long yx = td.base + node_offset(N, a, b, c);
         const T du = u[yx] - ux;
+        T ky[6];
+        load6(km + 6 * yx, ky);
         T s = 0;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) s = fma(st[(m * 16 + mask) * kNDir + d], kx[m] + km[m * nst + yx], s);
+        for (int m = 0; m < 6; ++m) s = fma(st[(m * 16 + mask) * kNDir + d], kx[m] + ky[m], s);
         y = fma(s, du, y);
         dg -= s;
       }

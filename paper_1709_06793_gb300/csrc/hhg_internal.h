@@ -125,7 +125,7 @@ struct Depth {
   std::vector<void*> allocations;
   // coefficient copies at this depth
   double* k16d = nullptr;  // bfloat16-rounded k held in double (outer residual of the bf16 solve)
-  // tensor coefficient (six terms, component-major: 6 x n_stored) and the
+  // tensor coefficient (six terms, node major: n_stored x 6) and the
   // six terms' reference stencils [slot][6][16][14] (set on first use)
   double* km64 = nullptr;
   float* km32 = nullptr;

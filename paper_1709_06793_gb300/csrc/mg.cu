@@ -67,6 +67,14 @@ __global__ void inject_kernel(DepthDev C, DepthDev F, const V* __restrict__ fine
   }
 }
 
+// the six k_m of one node, moved as one value by the injection kernel
+struct K6d {
+  double v[6];
+};
+struct K6f {
+  float v[6];
+};
+
 // k_m of the six-term split of a symmetric tensor (directions e1, e2, e3,
 // e1-e2, e1-e3, e2-e3): k_i = K_ii + sum_{j != i} K_ij, k_ij = -K_ij
 __global__ void tensor_split_kernel(const double* __restrict__ K6, long long n, double* __restrict__ km64,
@@ -75,9 +83,9 @@ __global__ void tensor_split_kernel(const double* __restrict__ K6, long long n, 
     const double K11 = K6[i], K22 = K6[n + i], K33 = K6[2 * n + i];
     const double K12 = K6[3 * n + i], K13 = K6[4 * n + i], K23 = K6[5 * n + i];
     const double v[6] = {K11 + K12 + K13, K22 + K12 + K23, K33 + K13 + K23, -K12, -K13, -K23};
-    for (int m = 0; m < 6; ++m) {
-      km64[m * n + i] = v[m];
-      km32[m * n + i] = (float)v[m];
+    for (int m = 0; m < 6; ++m) {  // node major: the six values of a node are contiguous
+      km64[6 * i + m] = v[m];
+      km32[6 * i + m] = (float)v[m];
     }
   }
 }
@@ -100,10 +108,10 @@ void set_tensor_coefficient(Mesh& m, const double* K6, cudaStream_t s) {
     Depth& C = m.depth[d];
     Depth& F = m.depth[d - 1];
     const int g = grid_for((long long)C.n_rows * 32, 256, 4096);
-    for (int t = 0; t < 6; ++t) {
-      inject_kernel<double><<<g, 256, 0, s>>>(C.dev, F.dev, F.km64 + t * F.n_stored, C.km64 + t * C.n_stored);
-      inject_kernel<float><<<g, 256, 0, s>>>(C.dev, F.dev, F.km32 + t * F.n_stored, C.km32 + t * C.n_stored);
-    }
+    inject_kernel<K6d><<<g, 256, 0, s>>>(C.dev, F.dev, reinterpret_cast<const K6d*>(F.km64),
+                                         reinterpret_cast<K6d*>(C.km64));
+    inject_kernel<K6f><<<g, 256, 0, s>>>(C.dev, F.dev, reinterpret_cast<const K6f*>(F.km32),
+                                         reinterpret_cast<K6f*>(C.km32));
     HHG_CUDA(cudaGetLastError());
   }
   m.tensor_set = true;
