@@ -78,6 +78,8 @@ struct Plane {
   typename Pair<T>::type cp[kTJ + 1];
   typename Pair<T>::type cm[kTJ + 2];
   int off[kTJ];  // tet-local offset of (i0-1, row) for the lane's rows (stores)
+  T fv[kTJ];     // f (and the previous Chebyshev update) at the lane's nodes,
+  T dv[kTJ];     // loaded when the plane is read, used when it is stored
 };
 
 struct OpPtrs {
@@ -90,18 +92,19 @@ struct OpPtrs {
   double omega, ca, cb;
 };
 
+// fv, dv: f and the previous Chebyshev update at the node (prefetched)
 template <class T, int MODE>
-__device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, const OpPtrs& p) {
+__device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, const OpPtrs& p, T fv, T dv) {
   if (MODE == OP_APPLY) {
     static_cast<T*>(p.out)[idx] = y;
   } else if (MODE == OP_RESID) {
-    static_cast<T*>(p.out)[idx] = __ldg(static_cast<const T*>(p.f) + idx) - y;
+    static_cast<T*>(p.out)[idx] = fv - y;
   } else if (MODE == OP_JACOBI) {
-    const T r = __ldg(static_cast<const T*>(p.f) + idx) - y;
+    const T r = fv - y;
     static_cast<T*>(p.out)[idx] = ux + (T)p.omega * r / diag;
   } else if (MODE == OP_CHEB) {
-    const T r = __ldg(static_cast<const T*>(p.f) + idx) - y;
-    const T prev = p.ca != 0.0 ? (T)p.ca * __ldg(static_cast<const T*>(p.d_in) + idx) : (T)0;
+    const T r = fv - y;
+    const T prev = p.ca != 0.0 ? (T)p.ca * dv : (T)0;
     const T dn = prev + (T)p.cb * r / diag;
     static_cast<T*>(p.d_out)[idx] = dn;
     static_cast<T*>(p.out)[idx] = ux + dn;
@@ -397,7 +400,19 @@ __device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 
   };
   auto read_next = [&](Plane<T>& P) {
     const unsigned char* sb = ring + st_r * SB;
+    const int pl = rh.q;
     read_plane<T, KT>(P, sb + lane_u, sb + lane_k, rh, bmod_u, bmod_k);
+    if (MODE == OP_RESID || MODE == OP_JACOBI || MODE == OP_CHEB) {
+      // f (and d_in) at the lane's nodes of this plane, needed one step later
+      const int lim_r = N - 1 - i - jb - pl;
+#pragma unroll
+      for (int r = 0; r < kTJ; ++r) {
+        const bool ok = r <= lim_r && pl >= k0;
+        P.fv[r] = ok ? __ldg(static_cast<const T*>(q.f) + P.off[r] + l + 1) : (T)0;
+        if (MODE == OP_CHEB)
+          P.dv[r] = ok && q.ca != 0.0 ? __ldg(static_cast<const T*>(q.d_in) + P.off[r] + l + 1) : (T)0;
+      }
+    }
     rh.next(N, jb - 1);
     st_r = st_r + 1 == kStages ? 0 : st_r + 1;
   };
@@ -412,7 +427,7 @@ __device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 
     const int lim_r = N - 1 - i - jb - pl;  // row r holds a volume node iff r <= lim_r
 #pragma unroll
     for (int r = 0; r < kTJ; ++r)
-      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r] + l + 1, q);
+      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r] + l + 1, q, P.fv[r], P.dv[r]);
   };
   auto step = [&](Plane<T>& P, Plane<T>& Q, Acc<T, DIAG>(&yP)[kTJ], Acc<T, DIAG>(&yQ)[kTJ], int qq) {
     __syncwarp();                  // every lane has read plane qq-2 before its stage is refilled
