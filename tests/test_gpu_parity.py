@@ -250,6 +250,15 @@ def test_dot_counts_each_unknown_once(H, case):
     assert abs(got - float(a @ b)) <= 1e-12 * max(1.0, abs(float(a @ b)))
 
 
+def test_fp32_dot_counts_each_unknown_once(H, case):
+    """FP32 vectors: groups of four products are summed in FP32 (2^-22
+    relative each), the groups in FP64."""
+    a, b = _f32(case.rand_or), _f32(np.where(case.dir, 0.0, np.cos(case.lm.coords[:, 0] * 3.0)))
+    got = H.hhg_dot(case.m.h, 0, case.dev(a, 1), case.dev(b, 1), 1)
+    want = float(a @ b)
+    assert abs(got - want) <= 1e-6 * float(np.abs(a) @ np.abs(b))
+
+
 def _hier(V, T, level, coarsest, kf, smoother="jacobi"):
     return O.Hierarchy(V, T, level, coarsest, k_func=kf, smoother=smoother)
 
