@@ -96,7 +96,8 @@ typedef struct {
     int smoother;        /* hhg_smoother */
     int nu1, nu2;        /* pre/post smoothing steps of the V-cycle */
     double omega;        /* Jacobi damping (default 2/3 if <= 0) */
-    double inner_rtol;   /* MIXED: relative residual reduction of each inner solve (default 1e-4) */
+    double inner_rtol;   /* MIXED: relative residual reduction of each inner solve (default 3e-5; never
+                            below half the outer tolerance) */
     int max_outer;       /* MIXED: max refinement steps (default 20) */
     int use_graph;       /* capture each CG iteration in a CUDA graph (1) or launch eagerly (0) */
     int op;              /* hhg_operator; HHG_OP_VOLFACE, HHG_OP_NODAL, HHG_OP_TENSOR need mode HHG_SOLVE_MG

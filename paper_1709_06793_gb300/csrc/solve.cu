@@ -1,6 +1,7 @@
 // Solver driver: GMG-preconditioned CG (scalars stay on the device, one CG
 // iteration captured as a CUDA graph) and FP64 iterative refinement around an
 // FP32 inner solve.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -256,7 +257,7 @@ static int solve_mg(Mesh& m, const hhg_solve_params& p, const double* f, double*
 int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg_solve_stats* st, cudaStream_t s) {
   hhg_solve_params p = p_in;
   if (p.omega <= 0) p.omega = 2.0 / 3.0;
-  if (p.inner_rtol <= 0) p.inner_rtol = 1e-4;
+  if (p.inner_rtol <= 0) p.inner_rtol = 3e-5;
   if (p.max_outer <= 0) p.max_outer = 20;
   if (p.maxit <= 0) p.maxit = 200;
   HHG_REQUIRE(p.tol > 0, "tol must be positive");
@@ -311,8 +312,10 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
       if (rel <= p.tol || total >= p.maxit) break;
       f64_to_f32_kernel<<<g, 256, 0, s>>>(r64, r32, n);
       HHG_CUDA(cudaMemsetAsync(d32, 0, n * 4, s));
-      // inner: reduce the residual by the factor inner_rtol
-      const double target = p.inner_rtol * p.inner_rtol * rr;
+      // inner: reduce the residual by the factor inner_rtol, but not below
+      // half the outer tolerance (the last inner solve stops where the outer
+      // one can finish instead of over-solving)
+      const double target = std::max(p.inner_rtol * p.inner_rtol * rr, 0.25 * p.tol * p.tol * nf2);
       PcgResult res = pcg(m, inner_dtype, p, d32, r32, target, p.maxit - total, s);
       total += res.its;
       if (p.smoother == HHG_SMOOTH_LEARNED && !(res.rr <= rr)) {

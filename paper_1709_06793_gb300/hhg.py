@@ -263,7 +263,7 @@ def hhg_dot(mesh, depth, x, y, dtype, stream=None):
 
 
 def hhg_solve(mesh, f, u, tol=1e-8, maxit=200, mode=HHG_SOLVE_FP64, smoother=HHG_SMOOTH_JACOBI, nu1=2, nu2=2,
-              omega=2.0 / 3.0, inner_rtol=1e-4, max_outer=20, use_graph=1, stream=None, raise_on_fail=True,
+              omega=2.0 / 3.0, inner_rtol=3e-5, max_outer=20, use_graph=1, stream=None, raise_on_fail=True,
               op=HHG_OP_SCALED):
     p = SolveParams(tol, maxit, mode, smoother, nu1, nu2, omega, inner_rtol, max_outer, use_graph, op)
     st = SolveStats()
