@@ -43,8 +43,11 @@ NCU_TRAFFIC = {"apply_sha": "e97dad7138f39bc0", "bytes": 263384064}
 
 
 def _kernel_sha():
-    p = os.path.join(ROOT, "paper_1709_06793_gb300", "csrc", "apply.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the scaled apply's sources (kernels and shared constants)."""
+    h = hashlib.sha256()
+    for f in ("apply.cu", "hhg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1709_06793_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
