@@ -1,0 +1,126 @@
+"""Parity at the full configured sizes, in the launch configuration the bench
+times, on sampled outputs: each sampled row of the GPU operator is compared
+with the oracle's one-row evaluator (row_apply, pinned against the element
+loop).  Inputs: u uniform in [-1, 1] from the node's canonical key (the same
+value on every copy and on both sides; 0 on Dirichlet nodes as the ABI
+requires), k from the coordinates; both rounded
+to FP32 as the kernels read them.  Tolerance as for the other FP32 applies:
+1e-6 of the largest sampled row value (sums of 14 FP32 products).
+
+Configurations: the level-8 6-tet cube (16.6 M unknowns; the bench's apply,
+autotuned as the bench does) and the batch of 48 random tetrahedra with
+levels drawn from 5..8 (one persistent launch for all of them).  A property
+that holds at any size closes the level-7 solve: the FP64 residual the test
+computes itself is within the requested 1e-8.
+"""
+import numpy as np
+import pytest
+
+from oracle import hhg_oracle as O
+from paper_1709_06793_gb300 import inputs as I
+from tests import hhg_testutil as U
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_06793_gb300 import build
+    build.build()
+    from paper_1709_06793_gb300 import hhg
+    return hhg
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def _sampled_parity(H, m, V, T, levels, kf, seed, n_vol=1500, n_face=600):
+    off, lev, n = m.layout(0)
+    nodes = U.stored_nodes(off, lev)
+    keys = U.stored_keys(T, nodes, lev)
+    u = _f32(I.uniform_from_keys(keys, seed))
+    xyz = m.coords(0)
+    k = _f32(kf(xyz))
+    H.hhg_set_coefficient(m.h, torch.tensor(k, device="cuda"))
+    ud = torch.tensor(u, device="cuda", dtype=torch.float32)
+    # inputs hold 0 on Dirichlet nodes (the ABI's contract): the residual of
+    # f = 1, u = 0 is 1 on the unknowns and 0 there
+    mask = torch.empty_like(ud)
+    H.hhg_residual(m.h, 0, torch.ones_like(ud), torch.zeros_like(ud), mask, H.HHG_F32)
+    ud *= mask
+    y = torch.empty_like(ud)
+    H.hhg_apply_scaled(m.h, 0, ud, y, H.HHG_F32)
+    torch.cuda.synchronize()
+    yg = y.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(seed)
+    t_, i_, j_, k_ = nodes.T
+    N_ = np.left_shift(1, lev[t_].astype(np.int64))
+    face = (i_ == 0) | (j_ == 0) | (k_ == 0) | (i_ + j_ + k_ == N_)
+    sample = np.concatenate([rng.choice(np.nonzero(~face)[0], n_vol, replace=False),
+                             rng.choice(np.nonzero(face)[0], n_face, replace=False)])
+    mm = O.MacroMesh(V, T)
+    Tn = np.asarray(T)
+
+    def field_u(gv, W, X):
+        Nn = int(W[0].sum())
+        return _f32(I.uniform_from_keys(I.node_keys(gv, W, Nn), seed))
+
+    def field_k(gv, W, X):
+        return _f32(kf(X))
+
+    want = np.empty(len(sample))
+    for q, (t, i, j, kk) in enumerate(nodes[sample]):
+        N = 1 << int(lev[t])
+        Wt = np.array([N - i - j - kk, i, j, kk])
+        sup, w = Tn[t][Wt > 0], Wt[Wt > 0]
+        want[q] = O.row_apply(mm, int(lev[t]), sup, w, field_u, field_k, "scaled")
+    got = yg[sample]
+    scale = np.max(np.abs(want))
+    assert scale > 0
+    err = np.max(np.abs(got - want)) / scale
+    assert err <= 1e-6, err
+    return err
+
+
+def test_level8_cube_fp32_apply_sampled(H):
+    """The bench's workload and launch configuration (autotuned work lists)."""
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, 8, 2)
+    off, lev, n = m.layout(0)
+    H.hhg_set_coefficient(m.h, torch.ones(n, device="cuda", dtype=torch.float64))
+    H.hhg_autotune(m.h, H.HHG_F32)
+    _sampled_parity(H, m, V, T, 8, I.k_cube, seed=11)
+    m.close()
+
+
+def test_48_random_tets_mixed_levels_fp32_apply_sampled(H):
+    V, T = I.random_tets(48, seed=1)
+    levels = np.random.default_rng(1).integers(5, 9, size=48)
+    m = H.Mesh(V, T, levels, 3)
+    _sampled_parity(H, m, V, T, levels, I.k_batched(1), seed=12, n_vol=1200, n_face=500)
+    m.close()
+
+
+def test_level7_mixed_solve_residual_full_size(H):
+    """FP32 GMG-CG with FP64 refinement on the 2.2 M-node level-7 cube: the
+    FP64 residual of the returned solution, computed here with the FP64
+    operator and dot, is within the requested tolerance."""
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, 7, 2)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_coefficient(m.h, torch.tensor(I.k_cube(xyz), device="cuda"))
+    fi = torch.tensor(I.f_cube_sine(xyz), device="cuda")
+    f = torch.empty_like(fi)
+    H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
+    u = torch.zeros(n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(m.h, f, u, tol=1e-8, mode=H.HHG_SOLVE_MIXED)
+    r = torch.empty_like(u)
+    H.hhg_residual(m.h, 0, f, u, r, H.HHG_F64)
+    rel = (H.hhg_dot(m.h, 0, r, r, H.HHG_F64) / H.hhg_dot(m.h, 0, f, f, H.HHG_F64)) ** 0.5
+    assert rel <= 1e-8 and abs(rel - st["rel_residual"]) <= 1e-3 * max(rel, 1e-16)
+    m.close()
