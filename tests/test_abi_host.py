@@ -128,3 +128,20 @@ def test_bad_arguments_are_reported(H):
     with pytest.raises(H.HHGError, match="host-only"):
         H.hhg_apply_scaled(m.h, 0, 1, 2, H.HHG_F32)
     m.close()
+
+
+def test_size_limits_and_empty_meshes_are_reported(H):
+    """Maximum level 10 (N = 1024: i, j, k fit the work lists' 11-bit
+    fields), coarsest level in [1, level], at least one tetrahedron."""
+    V, T = I.unit_tet()
+    m = H.Mesh(V, T, 10, 3, host_only=True)
+    assert m.layout(0)[2] == 1025 * 1026 * 1027 // 6 and m.ndepth == 8
+    m.close()
+    with pytest.raises(H.HHGError, match="level must be in"):
+        H.Mesh(V, T, 11, 3, host_only=True)
+    with pytest.raises(H.HHGError, match="level must be in"):
+        H.Mesh(V, T, 2, 3, host_only=True)
+    with pytest.raises(H.HHGError, match="coarsest_level"):
+        H.Mesh(V, T, 3, 0, host_only=True)
+    with pytest.raises(H.HHGError, match="at least"):
+        H.Mesh(V, np.zeros((0, 4), dtype=np.int32), 3, 2, host_only=True)

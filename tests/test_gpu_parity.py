@@ -541,3 +541,29 @@ def test_tensor_mg_solve_needs_no_scalar_coefficient(H):
     st = H.hhg_solve(m.h, f, u, tol=1e-9, maxit=60, mode=H.HHG_SOLVE_MG, nu1=3, nu2=3, op=H.HHG_OP_TENSOR)
     assert st["rel_residual"] <= 1e-9 and 0 < st["rho"] < 0.5
     m.close()
+
+
+def test_zero_sweeps_and_single_depth_mesh(H):
+    """Degenerate calls: zero smoothing sweeps leave u unchanged; a mesh whose
+    finest level is the coarsest one has one depth, and the solver is then
+    the dense coarse solve (exact to rounding)."""
+    mesh, level, coarsest, kf = MESHES["kuhn_cube_l4"]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    f = c.dev(c.rand_or, 0)
+    u = f.flip(0).contiguous()
+    u0 = u.clone()
+    H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_JACOBI, 0, 0.6, f, u, H.HHG_F64)
+    H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_CHEBYSHEV, 0, 0.6, f, u, H.HHG_F64)
+    torch.cuda.synchronize()
+    assert torch.equal(u, u0)
+    c.m.close()
+    c2 = Case(H, V, T, 2, 2, kf)
+    assert c2.m.ndepth == 1
+    f = c2.rand_or
+    u = torch.zeros(c2.n, device="cuda", dtype=torch.float64)
+    st = H.hhg_solve(c2.m.h, c2.dev(f, 0), u, tol=1e-12, mode=H.HHG_SOLVE_FP64)
+    A = c2.lm.system(c2.k_or, "scaled")
+    x = np.linalg.solve(A.toarray(), f[c2.lm.unknowns])
+    assert _rel(c2.back(u)[c2.lm.unknowns], x) <= 1e-10 and st["iterations"] <= 2
+    c2.m.close()
