@@ -204,7 +204,7 @@ struct Stage {
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void cp_async16(unsigned dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -229,67 +229,82 @@ struct Head {
   }
 };
 
-// Per-lane copy assignment (fixed for the whole kernel): lane L < kRows
-// copies row m = L of u, lane kRows <= L < 2 kRows row m = L - kRows of k.
-// One code path for both arrays (element size chosen per lane).
+// Copy assignment.  The tile's footprint in a plane is kRows row segments of
+// u and kRows of k.  For each array, lane = CH p + c (CH = chunks per row at
+// the worst alignment) copies chunk c of rows p, p + R, p + 2R, ... (R = 32 /
+// CH rows per round), so the 32 chunks of one cp.async instruction are
+// consecutive chunks of R rows (a few cache lines per instruction) rather
+// than one chunk of every row.
 struct CopyLane {
-  int m;         // staged row
-  int tri;       // m(m-1)/2
-  unsigned dst;  // byte offset of the row in a stage
-  int lg;        // log2(element bytes)
-  bool act;
+  int lane;
 };
 
 template <class T, class KT>
 __device__ __forceinline__ CopyLane copy_lane(int lane) {
-  CopyLane c;
-  c.act = lane < 2 * kRows;
-  const bool ku = lane < kRows;
-  c.m = ku ? lane : lane - kRows;
-  c.tri = c.m * (c.m - 1) / 2;
-  c.dst = ku ? (unsigned)(c.m * RowGeom<T>::stride * (int)sizeof(T))
-             : (unsigned)(Stage<T, KT>::u_bytes + c.m * RowGeom<KT>::stride * (int)sizeof(KT));
-  const int es = ku ? (int)sizeof(T) : (int)sizeof(KT);
-  c.lg = es == 8 ? 3 : (es == 4 ? 2 : 1);
-  return c;
+  return CopyLane{lane};
 }
 
-template <class T, class KT>
-constexpr int max_chunks() {
-  return RowGeom<T>::chunks > RowGeom<KT>::chunks ? RowGeom<T>::chunks : RowGeom<KT>::chunks;
+template <class E>
+constexpr int log2_bytes() {
+  return sizeof(E) == 8 ? 3 : (sizeof(E) == 4 ? 2 : 1);
 }
 
-// Stage plane H.q: the copying lane fetches its row's 16-byte chunks from the
-// aligned start at or before column i0-1 through column i0+16.  base = the
-// lane's array (u or k) at the tet base, in bytes; bm = tet base mod V; lim =
-// elements of the vector from the tet base on (chunks are cut there).
-template <class T, class KT>
-__device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const CopyLane& cl, int N, int jm1,
-                                            int lim, int bm, const unsigned char* __restrict__ base) {
-  if (!cl.act || jm1 + cl.m > N - H.q) return;  // idle lane, or the row is absent from this plane
-  constexpr int CH = max_chunks<T, KT>();
-  const int e = H.e0 + cl.m * H.A - cl.tri;      // element (i0-1, j0-1+m, q)
-  const int vm = (16 >> cl.lg) - 1;              // V - 1
-  const int mis = (e + bm) & vm;
-  const int a = e - mis;                         // aligned start (element)
-  const int nch = ((mis + kTileI + 1) >> (4 - cl.lg)) + 1;  // chunks through column i0+16
-  const unsigned char* src = base + ((long long)a << cl.lg);
-  const unsigned dst = stage + cl.dst;
-  if ((a + CH * (16 >> cl.lg)) <= lim) {  // away from the end of the vector: whole chunks
+// Rows m = 0..kRows-1 of one array (row m at byte offset RB + m * pitch of a
+// stage); rows m > mrows are absent from the plane.  Indices are counted
+// from the 16-byte boundary at or below the tet base (bm elements below it),
+// so a chunk's start is the row start rounded down to a multiple of V.
+template <class E, int RB>
+__device__ __forceinline__ void issue_rows(unsigned stage, const Head& H, int lane, int mrows, int lim, int bm,
+                                           const unsigned char* __restrict__ base) {
+  constexpr int CH = RowGeom<E>::chunks, R = 32 / CH, LG = log2_bytes<E>(), V = RowGeom<E>::V;
+  constexpr int PITCH = RowGeom<E>::stride * (int)sizeof(E);
+  const int p = lane / CH, c = lane - p * CH;
+  if (p >= R) return;  // lanes left over by the row size
+  // row p + Q starts Q (A - p) - Q (Q - 1) / 2 after row p
+  const int eb = H.e0 + p * H.A - p * (p - 1) / 2 + bm;
+  const int d = H.A - p;
+  const int pm = p - min(mrows, kRows - 1);  // row p + Q is staged iff pm + Q <= 0
+  const int thr = c * V - (kTileI + 1);      // chunk c reaches column i0+kTileI iff mis >= thr
+  const unsigned char* base_al = base - bm * (int)sizeof(E);
+  const unsigned dst0 = stage + (unsigned)(RB + p * PITCH + 16 * c);
+  // every chunk of the footprint ends before the end of the vector (row
+  // starts grow by at most A per row; a chunk ends < CH V elements after its
+  // row's start)
+  const bool inside = H.e0 + (kRows - 1) * H.A + CH * V <= lim;
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
-      if (c < nch) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * c), "l"(src + 16 * c) : "memory");
-  } else {
-    const int rem = (lim - a) << cl.lg;  // bytes left in the vector
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      if (c < nch) {
-        int nb = rem - 16 * c;
-        nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
-        cp_async16(dst + 16 * c, nb ? (const void*)(src + 16 * c) : (const void*)base, nb);
+  for (int r = 0; r * R < kRows; ++r) {
+    const int Q = r * R;
+    const int eg = eb + Q * d - Q * (Q - 1) / 2;  // row p + Q: element (i0-1, j, q)
+    const int mis = eg & (V - 1);
+    if (pm + Q <= 0 && mis >= thr) {
+      const int a = eg - mis;
+      const unsigned char* src = base_al + ((long long)a << LG) + 16 * c;
+      const unsigned dst = dst0 + Q * PITCH;
+      if (inside) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+      } else {
+        const long long left = (((long long)lim + bm - a) << LG) - 16 * c;  // bytes of the vector from the chunk on
+        if (left >= 16)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+        else
+          cp_async16(dst, left > 0 ? (const void*)src : (const void*)base, left > 0 ? (int)left : 0);
       }
     }
   }
+}
+
+// Stage plane H.q: row m (j = jm1 + m) of u and of k, from the aligned start
+// at or before column i0-1 through column i0+kTileI.  base_u / base_k = the
+// arrays at the tet base, in bytes; bm_u / bm_k = tet base mod V (elements
+// per chunk); lim = elements of the vector from the tet base on (chunks are
+// cut there and zero-filled beyond it).
+template <class T, class KT>
+__device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const CopyLane& cl, int N, int jm1,
+                                            int lim, int bm_u, int bm_k, const unsigned char* __restrict__ base_u,
+                                            const unsigned char* __restrict__ base_k) {
+  const int mrows = N - H.q - jm1;
+  issue_rows<T, 0>(stage, H, cl.lane, mrows, lim, bm_u, base_u);
+  issue_rows<KT, Stage<T, KT>::u_bytes>(stage, H, cl.lane, mrows, lim, bm_k, base_k);
 }
 
 template <class E>
@@ -363,12 +378,17 @@ __device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 
   const int bmod_k = (int)(td.base & (RowGeom<KT>::V - 1));
   const long long lim64 = D.n_stored - td.base;
   const int lim = lim64 > 0x7fffffffLL ? 0x7fffffff : (int)lim64;
+  // The read head counts elements from the 16-byte boundary at or below the
+  // tet base (bmod_u below it), so a staged row's misalignment is its head
+  // offset mod V; the node pointers carry the matching shift and the lane's
+  // column, so node (i, row) of a plane is ptr[row head offset].
+  const long long lb = td.base + l + 1 - bmod_u;
   OpPtrs q = p;
-  q.out = static_cast<T*>(p.out) + td.base;
-  if (MODE != OP_APPLY && MODE != OP_DIAG) q.f = static_cast<const T*>(p.f) + td.base;
+  q.out = static_cast<T*>(p.out) + lb;
+  if (MODE != OP_APPLY && MODE != OP_DIAG) q.f = static_cast<const T*>(p.f) + lb;
   if (MODE == OP_CHEB) {
-    q.d_in = static_cast<const T*>(p.d_in) + td.base;
-    q.d_out = static_cast<T*>(p.d_out) + td.base;
+    q.d_in = static_cast<const T*>(p.d_in) + lb;
+    q.d_out = static_cast<T*>(p.d_out) + lb;
   }
   // copy head (tile rows from j0-1) and read head (this half's rows from jb-1) at plane k0-1
   Head ch, rh;
@@ -381,67 +401,72 @@ __device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 
     ch.A = M - j0 + 2;
     ch.e0 = pl + (j0 - 1) * (M + 1) - (j0 - 1) * (j0 - 2) / 2 + (i0 - 1);
     rh.A = M - jb + 2;
-    rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1);
+    rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1) + bmod_u;
   }
   constexpr int SB = Stage<T, KT>::bytes;
-  // this lane's copy source (u or k at the tet base) and base alignment
-  const bool lane_copies_u = lane < kRows;
-  const unsigned char* cbase = lane_copies_u ? reinterpret_cast<const unsigned char*>(u)
-                                             : reinterpret_cast<const unsigned char*>(k);
-  const int cbm = lane_copies_u ? bmod_u : bmod_k;
+  static_assert(kStages == 4, "the march below is unrolled over a ring of 4 stages");
+  const unsigned char* cbase_u = reinterpret_cast<const unsigned char*>(u);
+  const unsigned char* cbase_k = reinterpret_cast<const unsigned char*>(k);
   const int lane_u = (kTJ * h * RowGeom<T>::stride + l) * (int)sizeof(T);  // row 4h, column l
   const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
-  int st_c = 0, st_r = 0;  // stage of the next plane to copy / to read
-  auto issue_next = [&]() {  // stage plane ch.q if the march needs it; one group per plane
-    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, cbm, cbase);
+  const unsigned char* ring_u = ring + lane_u;
+  const unsigned char* ring_k = ring + lane_k;
+  const int dk = bmod_k - bmod_u;
+  // stage plane ch.q into stage st if the march needs it; one group per plane
+  auto issue_next = [&](int st) {
+    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k);
     cp_async_commit();
     ch.next(N, j0 - 1);
-    st_c = st_c + 1 == kStages ? 0 : st_c + 1;
   };
-  auto read_next = [&](Plane<T>& P) {
-    const unsigned char* sb = ring + st_r * SB;
+  auto read_next = [&](Plane<T>& P, int st) {
     const int pl = rh.q;
-    read_plane<T, KT>(P, sb + lane_u, sb + lane_k, rh, bmod_u, bmod_k);
+    read_plane<T, KT>(P, ring_u + st * SB, ring_k + st * SB, rh, 0, dk);
     if (MODE == OP_RESID || MODE == OP_JACOBI || MODE == OP_CHEB) {
       // f (and d_in) at the lane's nodes of this plane, needed one step later
       const int lim_r = N - 1 - i - jb - pl;
 #pragma unroll
       for (int r = 0; r < kTJ; ++r) {
         const bool ok = r <= lim_r && pl >= k0;
-        P.fv[r] = ok ? __ldg(static_cast<const T*>(q.f) + P.off[r] + l + 1) : (T)0;
-        if (MODE == OP_CHEB)
-          P.dv[r] = ok && q.ca != 0.0 ? __ldg(static_cast<const T*>(q.d_in) + P.off[r] + l + 1) : (T)0;
+        P.fv[r] = ok ? __ldg(static_cast<const T*>(q.f) + P.off[r]) : (T)0;
+        if (MODE == OP_CHEB) P.dv[r] = ok && q.ca != 0.0 ? __ldg(static_cast<const T*>(q.d_in) + P.off[r]) : (T)0;
       }
     }
     rh.next(N, jb - 1);
-    st_r = st_r + 1 == kStages ? 0 : st_r + 1;
   };
-#pragma unroll
-  for (int t = 0; t < kStages - 1; ++t) issue_next();  // planes k0-1 .. k0+kStages-3
+  // planes k0-1 .. k0+1 into stages 0..2; the step for plane k0+t (t mod 4)
+  // then copies plane k0+t+2 into stage (3+t) mod 4 and reads stage (1+t) mod 4
+  issue_next(0);
+  issue_next(1);
+  issue_next(2);
   cp_async_wait<kStages - 2>();
   __syncwarp();
   Plane<T> X, Y;
-  read_next(X);  // plane k0-1
+  read_next(X, 0);  // plane k0-1
   Acc<T, DIAG> yX[kTJ], yY[kTJ];
   auto store = [&](const Plane<T>& P, Acc<T, DIAG>(&y)[kTJ], int pl) {
     const int lim_r = N - 1 - i - jb - pl;  // row r holds a volume node iff r <= lim_r
 #pragma unroll
     for (int r = 0; r < kTJ; ++r)
-      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r] + l + 1, q, P.fv[r], P.dv[r]);
+      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r], q, P.fv[r], P.dv[r]);
   };
-  auto step = [&](Plane<T>& P, Plane<T>& Q, Acc<T, DIAG>(&yP)[kTJ], Acc<T, DIAG>(&yQ)[kTJ], int qq) {
+  auto step = [&](auto tc, Plane<T>& P, Plane<T>& Q, Acc<T, DIAG>(&yP)[kTJ], Acc<T, DIAG>(&yQ)[kTJ], int qq) {
+    constexpr int t = decltype(tc)::value;
     __syncwarp();                  // every lane has read plane qq-2 before its stage is refilled
-    issue_next();                  // plane qq + kStages - 2
+    issue_next((3 + t) & 3);       // plane qq + 2
     cp_async_wait<kStages - 2>();  // this lane's copies of plane qq have landed
     __syncwarp();                  // ... and every other lane's
-    read_next(Q);                  // plane qq
+    read_next(Q, (1 + t) & 3);     // plane qq
     step_edges<T, DIAG>(P, Q, c, yP, yQ);
-    if (qq - 1 >= k0) store(P, yP, qq - 1);
+    if (t != 0 || qq - 1 >= k0) store(P, yP, qq - 1);
   };
-  for (int qq = k0; qq <= qend; qq += 2) {
-    step(X, Y, yX, yY, qq);
+  for (int qq = k0; qq <= qend; qq += 4) {
+    step(std::integral_constant<int, 0>{}, X, Y, yX, yY, qq);
     if (qq + 1 > qend) break;
-    step(Y, X, yY, yX, qq + 1);
+    step(std::integral_constant<int, 1>{}, Y, X, yY, yX, qq + 1);
+    if (qq + 2 > qend) break;
+    step(std::integral_constant<int, 2>{}, X, Y, yX, yY, qq + 2);
+    if (qq + 3 > qend) break;
+    step(std::integral_constant<int, 3>{}, Y, X, yY, yX, qq + 3);
   }
   cp_async_wait<0>();
   __syncwarp();
@@ -911,15 +936,13 @@ __device__ void nodal_item(const DepthDev& D, const T* __restrict__ elem, int4 i
     rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1);
   }
   constexpr int SB = Stage<T, KT>::bytes;
-  const bool lane_copies_u = lane < kRows;
-  const unsigned char* cbase = lane_copies_u ? reinterpret_cast<const unsigned char*>(u)
-                                             : reinterpret_cast<const unsigned char*>(k);
-  const int cbm = lane_copies_u ? bmod_u : bmod_k;
+  const unsigned char* cbase_u = reinterpret_cast<const unsigned char*>(u);
+  const unsigned char* cbase_k = reinterpret_cast<const unsigned char*>(k);
   const int lane_u = (kTJ * h * RowGeom<T>::stride + l) * (int)sizeof(T);
   const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
   int st_c = 0, st_r = 0;
   auto issue_next = [&]() {
-    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, cbm, cbase);
+    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k);
     cp_async_commit();
     ch.next(N, j0 - 1);
     st_c = st_c + 1 == kStages ? 0 : st_c + 1;
