@@ -57,6 +57,16 @@ __device__ __forceinline__ void edge1(P2 a, P2 b, T c, Acc<T, DIAG>& A) {
   A.y = fma(s, t.x, A.y);
   if (DIAG) A.d -= s;
 }
+// Two edges of row a with the same coefficient (opposite directions):
+// c [(k_a + k_b1)(u_b1 - u_a) + (k_a + k_b2)(u_b2 - u_a)] with one scaling.
+template <class T, bool DIAG, class P2>
+__device__ __forceinline__ void edge1x2(P2 a, P2 b1, P2 b2, T c, Acc<T, DIAG>& A) {
+  const P2 t1 = diffsum(a, b1);
+  const P2 t2 = diffsum(a, b2);
+  const T w = fma(t2.y, t2.x, t1.y * t1.x);
+  A.y = fma(c, w, A.y);
+  if (DIAG) A.d = fma(-c, t1.y + t2.y, A.d);
+}
 // Edge contribution to rows a (+F) and b (-F).
 template <class T, bool DIAG, class P2>
 __device__ __forceinline__ void edge2(P2 a, P2 b, T c, Acc<T, DIAG>& A, Acc<T, DIAG>& B) {
@@ -145,15 +155,13 @@ __device__ __forceinline__ void step_edges(const Plane<T>& P, const Plane<T>& Q,
 #pragma unroll
   for (int r = 0; r < kTJ; ++r) {
     const int m = r + 1;
-    edge1(Q.c0[m], Q.cp[m], c1, yQ[r]);  // +e1
-    edge1(Q.c0[m], Q.cm[m], c1, yQ[r]);  // -e1
+    edge1x2(Q.c0[m], Q.cp[m], Q.cm[m], c1, yQ[r]);  // +e1, -e1
     if (r + 1 < kTJ)
       edge2(Q.c0[m], Q.c0[m + 1], c2, yQ[r], yQ[r + 1]);  // +e2
     else
       edge1(Q.c0[m], Q.c0[m + 1], c2, yQ[r]);
     if (r == 0) edge1(Q.c0[m], Q.c0[m - 1], c2, yQ[r]);  // -e2
-    edge1(Q.c0[m], Q.cp[m - 1], c12, yQ[r]);             // e1-e2
-    edge1(Q.c0[m], Q.cm[m + 1], c12, yQ[r]);             // -(e1-e2)
+    edge1x2(Q.c0[m], Q.cp[m - 1], Q.cm[m + 1], c12, yQ[r]);  // e1-e2, -(e1-e2)
   }
 }
 
@@ -244,50 +252,72 @@ __device__ __forceinline__ CopyLane copy_lane(int lane) {
   return CopyLane{lane};
 }
 
-template <class E>
-constexpr int log2_bytes() {
-  return sizeof(E) == 8 ? 3 : (sizeof(E) == 4 ? 2 : 1);
+// elements a staged row can reach past its start (the last chunk's end)
+template <class T, class KT>
+constexpr int max_reach() {
+  return RowGeom<T>::chunks * RowGeom<T>::V > RowGeom<KT>::chunks * RowGeom<KT>::V ? RowGeom<T>::chunks * RowGeom<T>::V
+                                                                                   : RowGeom<KT>::chunks * RowGeom<KT>::V;
+}
+
+// 16-byte copy issued only where pred is set (no branch around it); the
+// destination is dst + OFF bytes.
+template <int OFF>
+__device__ __forceinline__ void cp_async16_if(bool pred, unsigned dst, const void* src) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %2, 0;\n @p cp.async.cg.shared.global [%0+%3], [%1], 16;\n}\n" ::"r"(dst),
+      "l"(src), "r"((int)pred), "n"(OFF)
+      : "memory");
+}
+
+// The copy rounds of issue_rows on the fast path: rows p + Q, Q = 0, R, 2R, ...
+template <class E, int RB, int Q>
+__device__ __forceinline__ void copy_rounds(int eb, int d, int pm, int thr, unsigned dst0, const E* lane_src) {
+  if constexpr (Q < kRows) {
+    constexpr int V = RowGeom<E>::V, R = 32 / RowGeom<E>::chunks;
+    constexpr int PITCH = RowGeom<E>::stride * (int)sizeof(E);
+    const int eg = eb + Q * d - Q * (Q - 1) / 2;  // row p + Q: element (i0-1, j, q)
+    const int mis = eg & (V - 1);
+    cp_async16_if<Q * PITCH>(pm + Q <= 0 && mis >= thr, dst0, lane_src + (eg - mis));
+    copy_rounds<E, RB, Q + R>(eb, d, pm, thr, dst0, lane_src);
+  }
 }
 
 // Rows m = 0..kRows-1 of one array (row m at byte offset RB + m * pitch of a
 // stage); rows m > mrows are absent from the plane.  Indices are counted
 // from the 16-byte boundary at or below the tet base (bm elements below it),
 // so a chunk's start is the row start rounded down to a multiple of V.
+// inside = every chunk of the footprint ends before the end of the vector
+// (then no chunk needs cutting, and the copies are predicated, branch-free).
 template <class E, int RB>
 __device__ __forceinline__ void issue_rows(unsigned stage, const Head& H, int lane, int mrows, int lim, int bm,
-                                           const unsigned char* __restrict__ base) {
-  constexpr int CH = RowGeom<E>::chunks, R = 32 / CH, LG = log2_bytes<E>(), V = RowGeom<E>::V;
+                                           const unsigned char* __restrict__ base, bool inside) {
+  constexpr int CH = RowGeom<E>::chunks, R = 32 / CH, V = RowGeom<E>::V;
   constexpr int PITCH = RowGeom<E>::stride * (int)sizeof(E);
   const int p = lane / CH, c = lane - p * CH;
-  if (p >= R) return;  // lanes left over by the row size
   // row p + Q starts Q (A - p) - Q (Q - 1) / 2 after row p
   const int eb = H.e0 + p * H.A - p * (p - 1) / 2 + bm;
   const int d = H.A - p;
-  const int pm = p - min(mrows, kRows - 1);  // row p + Q is staged iff pm + Q <= 0
-  const int thr = c * V - (kTileI + 1);      // chunk c reaches column i0+kTileI iff mis >= thr
-  const unsigned char* base_al = base - bm * (int)sizeof(E);
+  // row p + Q is staged iff pm + Q <= 0 (lanes left over by the row size never)
+  const int pm = p < R ? p - min(mrows, kRows - 1) : kRows;
+  const int thr = c * V - (kTileI + 1);  // chunk c reaches column i0+kTileI iff mis >= thr
+  const E* lane_src = reinterpret_cast<const E*>(base - bm * (int)sizeof(E) + 16 * c);
   const unsigned dst0 = stage + (unsigned)(RB + p * PITCH + 16 * c);
-  // every chunk of the footprint ends before the end of the vector (row
-  // starts grow by at most A per row; a chunk ends < CH V elements after its
-  // row's start)
-  const bool inside = H.e0 + (kRows - 1) * H.A + CH * V <= lim;
+  if (inside) {
+    copy_rounds<E, RB, 0>(eb, d, pm, thr, dst0, lane_src);
+  } else {
 #pragma unroll
-  for (int r = 0; r * R < kRows; ++r) {
-    const int Q = r * R;
-    const int eg = eb + Q * d - Q * (Q - 1) / 2;  // row p + Q: element (i0-1, j, q)
-    const int mis = eg & (V - 1);
-    if (pm + Q <= 0 && mis >= thr) {
-      const int a = eg - mis;
-      const unsigned char* src = base_al + ((long long)a << LG) + 16 * c;
-      const unsigned dst = dst0 + Q * PITCH;
-      if (inside) {
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-      } else {
-        const long long left = (((long long)lim + bm - a) << LG) - 16 * c;  // bytes of the vector from the chunk on
+    for (int r = 0; r * R < kRows; ++r) {
+      const int Q = r * R;
+      const int eg = eb + Q * d - Q * (Q - 1) / 2;
+      const int mis = eg & (V - 1);
+      if (pm + Q <= 0 && mis >= thr) {
+        const int a = eg - mis;
+        const long long left = ((long long)lim + bm - a - c * V) * (int)sizeof(E);  // bytes of the vector from the chunk on
+        const unsigned dst = dst0 + Q * PITCH;
         if (left >= 16)
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+          cp_async16(dst, lane_src + a, 16);
         else
-          cp_async16(dst, left > 0 ? (const void*)src : (const void*)base, left > 0 ? (int)left : 0);
+          cp_async16(dst, left > 0 ? (const void*)(lane_src + a) : (const void*)base, left > 0 ? (int)left : 0);
       }
     }
   }
@@ -303,8 +333,11 @@ __device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const
                                             int lim, int bm_u, int bm_k, const unsigned char* __restrict__ base_u,
                                             const unsigned char* __restrict__ base_k) {
   const int mrows = N - H.q - jm1;
-  issue_rows<T, 0>(stage, H, cl.lane, mrows, lim, bm_u, base_u);
-  issue_rows<KT, Stage<T, KT>::u_bytes>(stage, H, cl.lane, mrows, lim, bm_k, base_k);
+  // row starts grow by at most A per row; a chunk ends < CH V elements after its row's start
+  constexpr int reach = max_reach<T, KT>();
+  const bool inside = H.e0 + (kRows - 1) * H.A + reach <= lim;
+  issue_rows<T, 0>(stage, H, cl.lane, mrows, lim, bm_u, base_u, inside);
+  issue_rows<KT, Stage<T, KT>::u_bytes>(stage, H, cl.lane, mrows, lim, bm_k, base_k, inside);
 }
 
 template <class E>
