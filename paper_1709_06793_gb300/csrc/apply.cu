@@ -282,6 +282,23 @@ __device__ __forceinline__ void copy_rounds(int eb, int d, int pm, int thr, unsi
   }
 }
 
+// The same with u and k of one element size: the row geometry (and the tet
+// base's alignment) is shared, so one set of row arithmetic drives both copies.
+template <class E, int RBK, int Q>
+__device__ __forceinline__ void copy_rounds2(int eb, int d, int pm, int thr, unsigned dst0, const E* src_u,
+                                             const E* src_k) {
+  if constexpr (Q < kRows) {
+    constexpr int V = RowGeom<E>::V, R = 32 / RowGeom<E>::chunks;
+    constexpr int PITCH = RowGeom<E>::stride * (int)sizeof(E);
+    const int eg = eb + Q * d - Q * (Q - 1) / 2;
+    const int a = eg & ~(V - 1);
+    const bool pred = pm + Q <= 0 && eg - a >= thr;
+    cp_async16_if<Q * PITCH>(pred, dst0, src_u + a);
+    cp_async16_if<RBK + Q * PITCH>(pred, dst0, src_k + a);
+    copy_rounds2<E, RBK, Q + R>(eb, d, pm, thr, dst0, src_u, src_k);
+  }
+}
+
 // Rows m = 0..kRows-1 of one array (row m at byte offset RB + m * pitch of a
 // stage); rows m > mrows are absent from the plane.  Indices are counted
 // from the 16-byte boundary at or below the tet base (bm elements below it),
@@ -336,6 +353,20 @@ __device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const
   // row starts grow by at most A per row; a chunk ends < CH V elements after its row's start
   constexpr int reach = max_reach<T, KT>();
   const bool inside = H.e0 + (kRows - 1) * H.A + reach <= lim;
+  if constexpr (sizeof(T) == sizeof(KT)) {
+    if (inside) {  // one lane assignment for both arrays (bm_u == bm_k)
+      constexpr int CH = RowGeom<T>::chunks, R = 32 / CH, V = RowGeom<T>::V;
+      constexpr int PITCH = RowGeom<T>::stride * (int)sizeof(T);
+      const int p = cl.lane / CH, c = cl.lane - p * CH;
+      const int eb = H.e0 + p * H.A - p * (p - 1) / 2 + bm_u;
+      const int pm = p < R ? p - min(mrows, kRows - 1) : kRows;
+      const int shift = 16 * c - bm_u * (int)sizeof(T);
+      copy_rounds2<T, Stage<T, KT>::u_bytes, 0>(eb, H.A - p, pm, c * V - (kTileI + 1), stage + (unsigned)(p * PITCH + 16 * c),
+                                                reinterpret_cast<const T*>(base_u + shift),
+                                                reinterpret_cast<const T*>(base_k + shift));
+      return;
+    }
+  }
   issue_rows<T, 0>(stage, H, cl.lane, mrows, lim, bm_u, base_u, inside);
   issue_rows<KT, Stage<T, KT>::u_bytes>(stage, H, cl.lane, mrows, lim, bm_k, base_k, inside);
 }
