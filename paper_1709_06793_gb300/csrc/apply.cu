@@ -102,6 +102,12 @@ struct OpPtrs {
   double omega, ca, cb;
 };
 
+// Quotient of the damped Jacobi update: FP32 uses the fast division
+// intrinsic (within 2 ulp; the sweep is a preconditioner step, the outer
+// FP64 residual decides convergence), FP64 the correctly rounded one.
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+
 // fv, dv: f and the previous Chebyshev update at the node (prefetched)
 template <class T, int MODE>
 __device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, const OpPtrs& p, T fv, T dv) {
@@ -111,7 +117,7 @@ __device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, co
     static_cast<T*>(p.out)[idx] = fv - y;
   } else if (MODE == OP_JACOBI) {
     const T r = fv - y;
-    static_cast<T*>(p.out)[idx] = ux + (T)p.omega * r / diag;
+    static_cast<T*>(p.out)[idx] = ux + sdiv((T)p.omega * r, diag);
   } else if (MODE == OP_CHEB) {
     const T r = fv - y;
     const T prev = p.ca != 0.0 ? (T)p.ca * dv : (T)0;
@@ -596,7 +602,7 @@ __device__ void boundary_node(const DepthDev& D, const T* __restrict__ sten, int
   if (MODE == OP_RESID) {
     val = __ldg(static_cast<const T*>(p.f) + i0) - y;
   } else if (MODE == OP_JACOBI) {
-    val = ux + (T)p.omega * (__ldg(static_cast<const T*>(p.f) + i0) - y) / diag;
+    val = ux + sdiv((T)p.omega * (__ldg(static_cast<const T*>(p.f) + i0) - y), diag);
   } else if (MODE == OP_CHEB) {
     const T prev = p.ca != 0.0 ? (T)p.ca * __ldg(static_cast<const T*>(p.d_in) + i0) : (T)0;
     dval = prev + (T)p.cb * (__ldg(static_cast<const T*>(p.f) + i0) - y) / diag;
