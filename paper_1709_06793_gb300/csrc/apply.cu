@@ -10,14 +10,14 @@
 //     F = c_w (k_x + k_{x+w}) (u_{x+w} - u_x)
 // enters row x with + and row x+w with - (c is symmetric on the volume).
 //
-// Volume kernel (nodes strictly inside a macro tet).  A warp owns 4 tiles of
-// 8 consecutive i x 4 rows j; lane (g, l) owns column i = i0_g + l, rows
-// j0_g .. j0_g+3, and marches along k.  When plane q arrives it computes every
-// edge between planes q-1 and q and every edge inside plane q that touches its
-// nodes; after that the rows of plane q-1 are complete and are written.  Only
-// two planes of u and k live in registers; the neighbour columns i-1, i+1 are
-// loaded directly (L1 hits: the 8 lanes of a tile read contiguous memory).
-// Tiles of one warp share i0+j0 (anti-diagonal), so all 4 march equally far.
+// Volume kernel (nodes strictly inside a macro tet).  A warp owns a tile of
+// 16 consecutive i x 8 rows j and marches along k; lane (h, l) owns column
+// i = i0 + l, rows j0+4h .. j0+4h+3.  The tile's footprint of each plane is
+// staged in shared memory (see the staging section below).  When plane q
+// arrives a lane computes every edge between planes q-1 and q and every edge
+// inside plane q that touches its nodes; after that the rows of plane q-1 are
+// complete and are written.  Two planes of the lane's footprint live in
+// registers.
 #include <utility>
 
 #include "hhg_internal.h"
