@@ -52,3 +52,16 @@ def oracle_map(lm, nodes):
 
 def oracle_keys(lm):
     return I.node_keys(lm.node_gverts, lm.node_weights, lm.N)
+
+
+def node_index(offsets, t, i, j, k, N):
+    """Stored index of node (i, j, k) of tet t (all at refinement N): the
+    tet's offset plus planes 0..k-1, rows 0..j-1 of plane k, then i."""
+    t, i, j, k = (np.asarray(a, dtype=np.int64) for a in (t, i, j, k))
+
+    def tetnum(x):
+        return x * (x + 1) * (x + 2) // 6
+
+    M = N - k
+    return (np.asarray(offsets, dtype=np.int64)[t] + tetnum(N + 1) - tetnum(N + 1 - k)
+            + j * (M + 1) - j * (j - 1) // 2 + i)
