@@ -65,3 +65,16 @@ def node_index(offsets, t, i, j, k, N):
     M = N - k
     return (np.asarray(offsets, dtype=np.int64)[t] + tetnum(N + 1) - tetnum(N + 1 - k)
             + j * (M + 1) - j * (j - 1) // 2 + i)
+
+
+def lattice_field(X, scale):
+    """Rough reproducible input field in [-1, 1) from node coordinates that lie
+    on the lattice (1/scale) Z^3: an integer hash of the lattice point, so
+    every stored copy of a node gets the same value."""
+    q = np.rint(np.asarray(X, dtype=np.float64) * float(scale)).astype(np.int64)
+    h = (q[:, 0] * np.int64(73856093)) ^ (q[:, 1] * np.int64(19349663)) ^ (q[:, 2] * np.int64(83492791))
+    h = h * np.int64(-7046029254386353131)
+    h = h ^ ((h >> 29) & np.int64((1 << 35) - 1))
+    h = h * np.int64(-4658895280553007687)
+    v = ((h >> 20) & np.int64((1 << 40) - 1)).astype(np.float64) / float(1 << 40)
+    return 2.0 * v - 1.0

@@ -11,12 +11,19 @@ Configurations: the level-8 6-tet cube (16.6 M unknowns; the bench's apply,
 autotuned as the bench does) and the batch of 48 random tetrahedra with
 levels drawn from 5..8 (one persistent launch for all of them).  A property
 that holds at any size closes the level-7 solve: the FP64 residual the test
-computes itself is within the requested 1e-8.
+computes itself is within the requested 1e-8.  The learned-smoother
+configuration (level-7 cube, k = exp(2g) with g a Gaussian random field) is
+checked at full size through properties that hold at any size (its oracle
+parity is at level 4, tests/test_gpu_learned.py): the Jacobi-equivalent
+network reproduces a damped Jacobi sweep, any network is positively
+homogeneous in r, and the network trained here reaches 1e-8 (FP64 residual
+recomputed by the test) in fewer iterations than the plain V-cycle.
 """
 import numpy as np
 import pytest
 
 from oracle import hhg_oracle as O
+from oracle import learned_oracle as LO
 from paper_1709_06793_gb300 import inputs as I
 from tests import hhg_testutil as U
 
@@ -123,4 +130,55 @@ def test_level7_mixed_solve_residual_full_size(H):
     H.hhg_residual(m.h, 0, f, u, r, H.HHG_F64)
     rel = (H.hhg_dot(m.h, 0, r, r, H.HHG_F64) / H.hhg_dot(m.h, 0, f, f, H.HHG_F64)) ** 0.5
     assert rel <= 1e-8 and abs(rel - st["rel_residual"]) <= 1e-3 * max(rel, 1e-16)
+    m.close()
+
+
+def test_learned_level7_grf_properties(H):
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, 7, 2)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_coefficient(m.h, torch.tensor(I.k_learned()(xyz), device="cuda"))
+    mask = torch.empty(n, device="cuda", dtype=torch.float32)
+    H.hhg_residual(m.h, 0, torch.ones_like(mask), torch.zeros_like(mask), mask, H.HHG_F32)
+    # interface copies of a node carry one value (nodes lie on the 1/128 lattice)
+    r = torch.tensor(U.lattice_field(xyz, 128), device="cuda", dtype=torch.float32) * mask
+    # (1) the Jacobi-equivalent network (omega = 1/2, exact in BF16) is one damped Jacobi sweep from 0
+    H.hhg_learned_set_weights(m.h, LO.jacobi_weights(0.5).astype(np.float32), weights_bf16=1)
+    c = torch.zeros_like(r)
+    H.hhg_learned_forward(m.h, 0, r, c)
+    uj = torch.zeros_like(r)
+    H.hhg_smooth(m.h, 0, H.HHG_SMOOTH_JACOBI, 1, 0.5, r, uj, H.HHG_F32)
+    torch.cuda.synchronize()
+    cj, jj = c.double().cpu().numpy(), uj.double().cpu().numpy()
+    assert np.max(np.abs(cj - jj)) <= 1e-6 * np.max(np.abs(jj))
+    # (2) a random network: c(2.5 r) = 2.5 c(r) (no biases, ReLU)
+    w = np.random.default_rng(72).normal(0, 0.3, LO.N_W).astype(np.float32)
+    H.hhg_learned_set_weights(m.h, w, weights_bf16=1)
+    c1, c2 = torch.zeros_like(r), torch.zeros_like(r)
+    H.hhg_learned_forward(m.h, 0, r, c1)
+    H.hhg_learned_forward(m.h, 0, 2.5 * r, c2)
+    torch.cuda.synchronize()
+    a, b = c1.double().cpu().numpy(), c2.double().cpu().numpy()
+    assert np.max(np.abs(a)) > 0
+    assert np.max(np.abs(b - 2.5 * a)) <= 1e-6 * np.max(np.abs(b))
+    # (3) training on the GPU, then the solve with and without the network
+    st = H.hhg_learned_train(m.h, steps=120, pairs=4, lr=3e-3, max_depth=1, vcycle_pairs=2, init_noise=0.02,
+                             seed=3, weights_bf16=1)
+    assert st["accepted"] == 1
+    fi = torch.tensor(I.f_cube_sine(xyz), device="cuda")
+    f = torch.empty_like(fi)
+    H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
+    its = {}
+    for name, sm in (("plain", H.HHG_SMOOTH_JACOBI), ("learned", H.HHG_SMOOTH_LEARNED)):
+        u = torch.zeros(n, device="cuda", dtype=torch.float64)
+        s_ = H.hhg_solve(m.h, f, u, tol=1e-8, mode=H.HHG_SOLVE_MIXED, smoother=sm)
+        res = torch.empty_like(u)
+        H.hhg_residual(m.h, 0, f, u, res, H.HHG_F64)
+        rel = (H.hhg_dot(m.h, 0, res, res, H.HHG_F64) / H.hhg_dot(m.h, 0, f, f, H.HHG_F64)) ** 0.5
+        assert rel <= 1e-8, (name, rel)
+        its[name] = s_["iterations"]
+        if name == "learned":
+            assert s_["smoother_used"] == H.HHG_SMOOTH_LEARNED
+    assert its["learned"] < its["plain"], its
     m.close()

@@ -44,16 +44,10 @@ def _f32(x):
 
 
 def _u_field(X):
-    """Rough reproducible field in [-1, 1): an integer hash of the node's
-    coordinates on the 1/1024 lattice (every level-9 node of this mesh lies on
-    it, and both sides form the coordinates exactly)."""
-    q = np.rint(np.asarray(X, dtype=np.float64) * 1024.0).astype(np.int64)
-    h = (q[:, 0] * np.int64(73856093)) ^ (q[:, 1] * np.int64(19349663)) ^ (q[:, 2] * np.int64(83492791))
-    h = h * np.int64(-7046029254386353131)
-    h = h ^ ((h >> 29) & np.int64((1 << 35) - 1))
-    h = h * np.int64(-4658895280553007687)
-    v = ((h >> 20) & np.int64((1 << 40) - 1)).astype(np.float64) / float(1 << 40)
-    return 2.0 * v - 1.0
+    """Rough field in [-1, 1) from the node's coordinates (every level-9 node
+    of this mesh lies on the 1/1024 lattice, and both sides form the
+    coordinates exactly)."""
+    return U.lattice_field(X, 1024)
 
 
 def _k_field(X):
