@@ -656,10 +656,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) scaled_op_kernel(
   }
 }
 
-// Interface rows on their own: one thread per unique interface node.  Runs on
-// the mesh's side stream concurrently with the volume kernel (its few
-// registers and no shared memory let it fill the warp slots the volume
-// kernel leaves free), instead of as chunks inside the volume kernel's loop.
+// Interface rows on their own: one thread per unique boundary node, launched
+// on the mesh's side stream ahead of the volume kernel (its blocks take the
+// SMs first and the persistent volume blocks start as they drain), instead
+// of as chunks inside the volume kernel's loop.
 template <class T, class KT, int MODE>
 __global__ void __launch_bounds__(128) boundary_only_kernel(DepthDev D, OpPtrs p, int n_b) {
   const T* sten;
