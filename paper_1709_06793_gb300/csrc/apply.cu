@@ -352,26 +352,28 @@ __device__ __forceinline__ void issue_rows(unsigned stage, const Head& H, int la
 // per chunk); lim = elements of the vector from the tet base on (chunks are
 // cut there and zero-filled beyond it).
 template <class T, class KT>
+// want = the march needs this plane (otherwise nothing is copied; the
+// arithmetic runs predicated off rather than behind a branch).
 __device__ __forceinline__ void issue_plane(unsigned stage, const Head& H, const CopyLane& cl, int N, int jm1,
                                             int lim, int bm_u, int bm_k, const unsigned char* __restrict__ base_u,
-                                            const unsigned char* __restrict__ base_k) {
-  const int mrows = N - H.q - jm1;
+                                            const unsigned char* __restrict__ base_k, bool want) {
+  const int mrows = want ? N - H.q - jm1 : -1;
   // row starts grow by at most A per row; a chunk ends < CH V elements after its row's start
   constexpr int reach = max_reach<T, KT>();
   const bool inside = H.e0 + (kRows - 1) * H.A + reach <= lim;
   if constexpr (sizeof(T) == sizeof(KT)) {
-    if (inside) {  // one lane assignment for both arrays (bm_u == bm_k)
-      constexpr int CH = RowGeom<T>::chunks, R = 32 / CH, V = RowGeom<T>::V;
-      constexpr int PITCH = RowGeom<T>::stride * (int)sizeof(T);
-      const int p = cl.lane / CH, c = cl.lane - p * CH;
-      const int eb = H.e0 + p * H.A - p * (p - 1) / 2 + bm_u;
-      const int pm = p < R ? p - min(mrows, kRows - 1) : kRows;
-      const int shift = 16 * c - bm_u * (int)sizeof(T);
-      copy_rounds2<T, Stage<T, KT>::u_bytes, 0>(eb, H.A - p, pm, c * V - (kTileI + 1), stage + (unsigned)(p * PITCH + 16 * c),
-                                                reinterpret_cast<const T*>(base_u + shift),
-                                                reinterpret_cast<const T*>(base_k + shift));
-      return;
-    }
+    // one lane assignment for both arrays (bm_u == bm_k); only a footprint
+    // that reaches the end of the vector takes the checked path below
+    constexpr int CH = RowGeom<T>::chunks, R = 32 / CH, V = RowGeom<T>::V;
+    constexpr int PITCH = RowGeom<T>::stride * (int)sizeof(T);
+    const int p = cl.lane / CH, c = cl.lane - p * CH;
+    const int eb = H.e0 + p * H.A - p * (p - 1) / 2 + bm_u;
+    const int pm = p < R && inside ? p - min(mrows, kRows - 1) : kRows;
+    const int shift = 16 * c - bm_u * (int)sizeof(T);
+    copy_rounds2<T, Stage<T, KT>::u_bytes, 0>(eb, H.A - p, pm, c * V - (kTileI + 1), stage + (unsigned)(p * PITCH + 16 * c),
+                                              reinterpret_cast<const T*>(base_u + shift),
+                                              reinterpret_cast<const T*>(base_k + shift));
+    if (inside) return;
   }
   issue_rows<T, 0>(stage, H, cl.lane, mrows, lim, bm_u, base_u, inside);
   issue_rows<KT, Stage<T, KT>::u_bytes>(stage, H, cl.lane, mrows, lim, bm_k, base_k, inside);
@@ -484,7 +486,7 @@ __device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 
   const int dk = bmod_k - bmod_u;
   // stage plane ch.q into stage st if the march needs it; one group per plane
   auto issue_next = [&](int st) {
-    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k);
+    issue_plane<T, KT>(ring_s + st * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k, ch.q <= qend);
     cp_async_commit();
     ch.next(N, j0 - 1);
   };
@@ -1012,7 +1014,7 @@ __device__ void nodal_item(const DepthDev& D, const T* __restrict__ elem, int4 i
   const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
   int st_c = 0, st_r = 0;
   auto issue_next = [&]() {
-    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k);
+    if (ch.q <= qend) issue_plane<T, KT>(ring_s + st_c * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k, true);
     cp_async_commit();
     ch.next(N, j0 - 1);
     st_c = st_c + 1 == kStages ? 0 : st_c + 1;
