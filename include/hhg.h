@@ -195,7 +195,11 @@ int hhg_set_coefficient(hhg_mesh mesh, const double* k_dev, void* stream);
 
 /* y = A_s(k) u: the scaled operator (Sec. 6.1) at `depth` on all active tets.
  * u_dev, y_dev: device arrays of the depth's stored length, element type of
- * `dtype`; they must not overlap. */
+ * `dtype`; they must not overlap.  Rows of Dirichlet nodes are 0 and all
+ * copies of an interface node get the same value.  The interface rows run on
+ * a library stream forked from `stream` with an event and joined to it before
+ * the call returns (so the call may be captured in a CUDA graph); one mesh
+ * must not be used from two streams at once. */
 int hhg_apply_scaled(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
 
 /* y = A_n(k) u: the nodal-integration operator of eq. "standardfe", computed
