@@ -87,3 +87,31 @@ def test_tensor_manufactured_solution_converges_at_second_order():
         err.append(O.discrete_l2(lm, e))
     # pre-asymptotic on these levels: the ratio grows towards 4 (nodal integration behaves the same)
     assert 3.0 <= err[0] / err[1] < err[1] / err[2] <= 4.6 and err[1] / err[2] >= 3.5
+
+
+@pytest.mark.parametrize("mesh,level", [(I.cube12, 3), (I.regular_tet, 3)])
+def test_each_term_volume_stencil_is_point_symmetric(mesh, level):
+    """For every term m (constant k_m = 1) the row of a node strictly inside a
+    macro tetrahedron has equal entries towards x + w and x - w, for all 14
+    directions w.  Hence an edge weight of a volume row is B_d(x) + B_d(x+w_d)
+    with B_d(z) = sum_m c^m_d k_m(z)/2 for the 7 positive directions only."""
+    V, T = mesh()
+    lm = O.LevelMesh(O.MacroMesh(V, T), level)
+    N = lm.N
+    dirs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, -1, 0), (1, 0, -1), (0, 1, -1), (1, -1, 1)]
+    for m in range(6):
+        km = np.zeros((lm.n, 6))
+        km[:, m] = 1.0
+        A = O.tensor_matrix(lm, km, "scaled").tocsr()
+        checked = 0
+        for t in range(len(lm.macro.T)):
+            L = lm.local[t]
+            for i in range(1, N):
+                for j in range(1, N - i):
+                    for k in range(1, N - i - j):
+                        x = L[i, j, k]
+                        for (a, b, c) in dirs:
+                            p, q = L[i + a, j + b, k + c], L[i - a, j - b, k - c]
+                            assert abs(A[x, p] - A[x, q]) <= 1e-14 * max(1.0, abs(A[x, x]))
+                        checked += 1
+        assert checked > 0
