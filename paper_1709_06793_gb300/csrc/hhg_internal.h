@@ -131,6 +131,11 @@ struct Depth {
   float* km32 = nullptr;
   const double* tsten64 = nullptr;
   const float* tsten32 = nullptr;
+  // per-direction node weights of the tensor operator's volume rows
+  // (B_d = sum_m c^m_d k_m for the 7 positive directions d of the volume
+  // stencil; direction major: 7 x n_stored), set with the tensor coefficient
+  double* tb64 = nullptr;
+  float* tb32 = nullptr;
   double* k64 = nullptr;
   float* k32 = nullptr;
   __nv_bfloat16* k16 = nullptr;
@@ -273,6 +278,7 @@ void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const O
 // nodal-integration operator in the modes above (dinv: 1/diag, 0 on Dirichlet nodes; tmp: a scratch vector)
 void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s);
 // scaled operator of the tensor coefficient (M = 6) in the modes above (py, pd: scratch vectors)
+void compute_tensor_weights(Mesh& m, cudaStream_t s);
 void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, void* py, void* pd,
                       cudaStream_t s);
 void ensure_tensor_stencils(Mesh& m);
