@@ -115,3 +115,40 @@ def test_each_term_volume_stencil_is_point_symmetric(mesh, level):
                             assert abs(A[x, p] - A[x, q]) <= 1e-14 * max(1.0, abs(A[x, x]))
                         checked += 1
         assert checked > 0
+
+
+def test_volume_rows_from_per_direction_node_weights():
+    """The form the volume rows are evaluated in: with c^m_d = (1/2) of term
+    m's constant-coefficient entry towards +w_d (d = the 7 positive
+    directions) and B_d(z) = sum_m c^m_d k_m(z), every off-diagonal entry of a
+    volume row of the variable-K operator is B_d(x) + B_d(x +- w_d)."""
+    V, T = I.cube12()
+    lm = O.LevelMesh(O.MacroMesh(V, T), 3)
+    N = lm.N
+    km = O.tensor_split(I.K_tensor(lm.coords))
+    A = O.tensor_matrix(lm, km, "scaled").tocsr()
+    dirs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, -1, 0), (1, 0, -1), (0, 1, -1), (1, -1, 1)]
+    ones = []
+    for m in range(6):
+        e = np.zeros((lm.n, 6))
+        e[:, m] = 1.0
+        ones.append(O.tensor_matrix(lm, e, "scaled").tocsr())
+    checked = 0
+    for t in range(len(lm.macro.T)):
+        L = lm.local[t]
+        # the term coefficients of this tet's volume stencil, read at one interior node
+        i0, j0, k0 = 1, 1, 1
+        x0 = L[i0, j0, k0]
+        c = np.array([[0.5 * ones[m][x0, L[i0 + a, j0 + b, k0 + cc]] for (a, b, cc) in dirs] for m in range(6)])
+        B = km @ c  # (n, 7): B_d at every node
+        for i in range(1, N):
+            for j in range(1, N - i):
+                for k in range(1, N - i - j):
+                    x = L[i, j, k]
+                    for d, (a, b, cc) in enumerate(dirs):
+                        for s in (1, -1):
+                            y = L[i + s * a, j + s * b, k + s * cc]
+                            want = A[x, y]
+                            assert abs(B[x, d] + B[y, d] - want) <= 1e-13 * abs(A[x, x])
+                    checked += 1
+    assert checked > 0
