@@ -1,13 +1,22 @@
-// Operator kernels beside the stencil-scaled one (scaled.cu): the
-// nodal-integration apply (eq. "standardfe", eq. "onTheFlyStencil", Sec. 6.2)
-// with its diagonal and epilogues, the "scale Vol+Face" row replacement
-// (Sec. 5, eq. "modst") and the consistent mass matrix.
+// Operator kernels: the stencil-scaled apply (Sec. 6.1) fused with residual,
+// damped Jacobi and Chebyshev updates, and the nodal-integration apply
+// (eq. "onTheFlyStencil", Sec. 6.2).
 //
-// The staged nodal kernel shares its staging scheme with the scaled tile
-// kernel's first form: a warp owns a tile of 16 consecutive i x 8 rows j and
-// marches along k; lane (h, l) owns column i = i0 + l, rows j0+4h .. j0+4h+3;
-// the tile's footprint of each plane is staged in shared memory (see the
-// staging section below) and three planes of the lane's footprint live in
+// Scaled operator, row of node x:
+//     (A u)_x = sum_{d} c_d^{prim(x)} (k_x + k_{x+w_d}) (u_{x+w_d} - u_x)
+// with c = (1/2) reference stencil of x's primitive (the factor 1/2 folded in
+// at setup, Sec. 6.1) and the diagonal -sum_d c_d (k_x + k_{x+w_d}) implied by
+// the zero row sum.  Written per edge (x, x+w): the flux
+//     F = c_w (k_x + k_{x+w}) (u_{x+w} - u_x)
+// enters row x with + and row x+w with - (c is symmetric on the volume).
+//
+// Volume kernel (nodes strictly inside a macro tet).  A warp owns a tile of
+// 16 consecutive i x 8 rows j and marches along k; lane (h, l) owns column
+// i = i0 + l, rows j0+4h .. j0+4h+3.  The tile's footprint of each plane is
+// staged in shared memory (see the staging section below).  When plane q
+// arrives a lane computes every edge between planes q-1 and q and every edge
+// inside plane q that touches its nodes; after that the rows of plane q-1 are
+// complete and are written.  Two planes of the lane's footprint live in
 // registers.
 #include <utility>
 
@@ -30,6 +39,47 @@ __device__ __forceinline__ float ldk(const float* p, long long i) { return __ldg
 __device__ __forceinline__ double ldk(const double* p, long long i) { return __ldg(p + i); }
 __device__ __forceinline__ float ldk(const __nv_bfloat16* p, long long i) { return __bfloat162float(__ldg(p + i)); }
 
+// (u_b - u_a, k_b + k_a) in one packed FMA for fp32.
+__device__ __forceinline__ float2 diffsum(float2 a, float2 b) { return __ffma2_rn(a, make_float2(-1.f, 1.f), b); }
+__device__ __forceinline__ double2 diffsum(double2 a, double2 b) { return make_double2(b.x - a.x, b.y + a.y); }
+
+template <class T, bool DIAG>
+struct Acc {
+  T y = 0;
+  T d = 0;
+};
+
+// Edge contribution to row a only.
+template <class T, bool DIAG, class P2>
+__device__ __forceinline__ void edge1(P2 a, P2 b, T c, Acc<T, DIAG>& A) {
+  const P2 t = diffsum(a, b);
+  const T s = c * t.y;
+  A.y = fma(s, t.x, A.y);
+  if (DIAG) A.d -= s;
+}
+// Two edges of row a with the same coefficient (opposite directions):
+// c [(k_a + k_b1)(u_b1 - u_a) + (k_a + k_b2)(u_b2 - u_a)] with one scaling.
+template <class T, bool DIAG, class P2>
+__device__ __forceinline__ void edge1x2(P2 a, P2 b1, P2 b2, T c, Acc<T, DIAG>& A) {
+  const P2 t1 = diffsum(a, b1);
+  const P2 t2 = diffsum(a, b2);
+  const T w = fma(t2.y, t2.x, t1.y * t1.x);
+  A.y = fma(c, w, A.y);
+  if (DIAG) A.d = fma(-c, t1.y + t2.y, A.d);
+}
+// Edge contribution to rows a (+F) and b (-F).
+template <class T, bool DIAG, class P2>
+__device__ __forceinline__ void edge2(P2 a, P2 b, T c, Acc<T, DIAG>& A, Acc<T, DIAG>& B) {
+  const P2 t = diffsum(a, b);
+  const T s = c * t.y;
+  A.y = fma(s, t.x, A.y);
+  B.y = fma(-s, t.x, B.y);
+  if (DIAG) {
+    A.d -= s;
+    B.d -= s;
+  }
+}
+
 // Register state of one plane of a lane's column footprint: rows m = 0..kTJ+1
 // (j = j0-1+m) at column offsets 0, +1 (m = 0..kTJ) and -1 (m = 1..kTJ+1).
 template <class T>
@@ -51,6 +101,75 @@ struct OpPtrs {
   void* d_out;
   double omega, ca, cb;
 };
+
+// Quotient of the damped Jacobi update: FP32 uses the fast division
+// intrinsic (within 2 ulp; the sweep is a preconditioner step, the outer
+// FP64 residual decides convergence), FP64 the correctly rounded one.
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+
+// fv, dv: f and the previous Chebyshev update at the node (prefetched)
+template <class T, int MODE>
+__device__ __forceinline__ void finish_node(T y, T diag, T ux, long long idx, const OpPtrs& p, T fv, T dv) {
+  if (MODE == OP_APPLY) {
+    static_cast<T*>(p.out)[idx] = y;
+  } else if (MODE == OP_RESID) {
+    static_cast<T*>(p.out)[idx] = fv - y;
+  } else if (MODE == OP_JACOBI) {
+    const T r = fv - y;
+    static_cast<T*>(p.out)[idx] = ux + sdiv((T)p.omega * r, diag);
+  } else if (MODE == OP_CHEB) {
+    const T r = fv - y;
+    const T prev = p.ca != 0.0 ? (T)p.ca * dv : (T)0;
+    const T dn = prev + (T)p.cb * r / diag;
+    static_cast<T*>(p.d_out)[idx] = dn;
+    static_cast<T*>(p.out)[idx] = ux + dn;
+  } else {  // OP_DIAG
+    static_cast<T*>(p.out)[idx] = diag;
+  }
+}
+
+// One march step: plane P (q-1) is complete in registers, plane Q (q) was
+// just loaded.  Adds all edges P-Q touching the lane's nodes and all in-plane
+// edges of Q; yP (rows of plane q-1) becomes final, yQ gets its first part.
+template <class T, bool DIAG>
+__device__ __forceinline__ void step_edges(const Plane<T>& P, const Plane<T>& Q, const T (&c)[7],
+                                           Acc<T, DIAG> (&yP)[kTJ], Acc<T, DIAG> (&yQ)[kTJ]) {
+  const T c1 = c[0], c2 = c[1], c3 = c[2], c12 = c[3], c13 = c[4], c23 = c[5], cg = c[6];
+#pragma unroll
+  for (int r = 0; r < kTJ; ++r) yQ[r] = Acc<T, DIAG>{};
+  // (A) edges between planes q-1 and q
+#pragma unroll
+  for (int r = 0; r < kTJ; ++r) {
+    const int m = r + 1;
+    edge2(P.c0[m], Q.c0[m], c3, yP[r], yQ[r]);  // +e3
+    edge1(P.c0[m], Q.cm[m], c13, yP[r]);        // -(e1-e3)
+    if (r >= 1)
+      edge2(P.c0[m], Q.c0[m - 1], c23, yP[r], yQ[r - 1]);  // -(e2-e3)
+    else
+      edge1(P.c0[m], Q.c0[m - 1], c23, yP[r]);
+    edge1(P.c0[m], Q.cp[m - 1], cg, yP[r]);  // e1-e2+e3
+  }
+#pragma unroll
+  for (int r = 0; r < kTJ; ++r) {
+    const int m = r + 1;
+    edge1(Q.c0[m], P.cp[m], c13, yQ[r]);                  // e1-e3
+    if (r == kTJ - 1) edge1(Q.c0[m], P.c0[m + 1], c23, yQ[r]);  // e2-e3
+    edge1(Q.c0[m], P.cm[m + 1], cg, yQ[r]);               // -(e1-e2+e3)
+  }
+  // (B) edges inside plane q
+#pragma unroll
+  for (int r = 0; r < kTJ; ++r) {
+    const int m = r + 1;
+    edge1x2(Q.c0[m], Q.cp[m], Q.cm[m], c1, yQ[r]);  // +e1, -e1
+    if (r + 1 < kTJ)
+      edge2(Q.c0[m], Q.c0[m + 1], c2, yQ[r], yQ[r + 1]);  // +e2
+    else
+      edge1(Q.c0[m], Q.c0[m + 1], c2, yQ[r]);
+    if (r == 0) edge1(Q.c0[m], Q.c0[m - 1], c2, yQ[r]);  // -e2
+    edge1x2(Q.c0[m], Q.cp[m - 1], Q.cm[m + 1], c12, yQ[r]);  // e1-e2, -(e1-e2)
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Volume kernel with shared-memory staging.
@@ -303,6 +422,343 @@ __device__ __forceinline__ void read_plane(Plane<T>& Q, const unsigned char* sta
     if (mm >= 1) Q.cm[mm] = P2{us[0], kv0};
     Q.c0[mm] = P2{us[1], kv1};
     if (mm <= kTJ) Q.cp[mm] = P2{us[2], kv2};
+  }
+}
+
+// One warp item: tile (i0, j0) of one tet, planes k0..k1 of its k-march.
+template <class T, class KT, int MODE>
+__device__ void volume_item(const DepthDev& D, const T* __restrict__ sten, int4 item, int lane, const OpPtrs& p,
+                            unsigned char* ring, unsigned ring_s, const CopyLane& cl) {
+  constexpr bool DIAG = (MODE == OP_JACOBI || MODE == OP_CHEB || MODE == OP_DIAG);
+  if (item.z < item.y) return;  // padding item: no planes
+  const unsigned tile = (unsigned)item.x;
+  const int slot = (int)(tile >> 20);
+  const int j0 = (int)((tile >> 10) & 1023u), i0 = (int)(tile & 1023u);
+  const int k0 = item.y;
+  const TetDev td = D.tets[slot];
+  const int N = td.N;
+  const int qend = min(item.z + 1, N - (i0 + j0));
+  const int h = lane / kTileI, l = lane % kTileI;
+  const int i = i0 + l;
+  const int jb = j0 + kTJ * h;  // first row of this row group
+  T c[7];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) c[d] = sten[slot * 16 * kNDir + d];  // volume row (mask 0)
+  const T* u = static_cast<const T*>(p.u) + td.base;
+  const KT* k = static_cast<const KT*>(p.k) + td.base;
+  const int bmod_u = (int)(td.base & (RowGeom<T>::V - 1));
+  const int bmod_k = (int)(td.base & (RowGeom<KT>::V - 1));
+  const long long lim64 = D.n_stored - td.base;
+  const int lim = lim64 > 0x7fffffffLL ? 0x7fffffff : (int)lim64;
+  // The read head counts elements from the 16-byte boundary at or below the
+  // tet base (bmod_u below it), so a staged row's misalignment is its head
+  // offset mod V; the node pointers carry the matching shift and the lane's
+  // column, so node (i, row) of a plane is ptr[row head offset].
+  const long long lb = td.base + l + 1 - bmod_u;
+  OpPtrs q = p;
+  q.out = static_cast<T*>(p.out) + lb;
+  if (MODE != OP_APPLY && MODE != OP_DIAG) q.f = static_cast<const T*>(p.f) + lb;
+  if (MODE == OP_CHEB) {
+    q.d_in = static_cast<const T*>(p.d_in) + lb;
+    q.d_out = static_cast<T*>(p.d_out) + lb;
+  }
+  // copy head (tile rows from j0-1) and read head (this half's rows from jb-1) at plane k0-1
+  Head ch, rh;
+  {
+    const int qq = k0 - 1;
+    const int M = N - qq;
+    ch.q = rh.q = qq;
+    ch.Psz = rh.Psz = (M + 1) * (M + 2) / 2;
+    const int pl = (int)(tetnum(N + 1) - tetnum(N + 1 - qq));
+    ch.A = M - j0 + 2;
+    ch.e0 = pl + (j0 - 1) * (M + 1) - (j0 - 1) * (j0 - 2) / 2 + (i0 - 1);
+    rh.A = M - jb + 2;
+    rh.e0 = pl + (jb - 1) * (M + 1) - (jb - 1) * (jb - 2) / 2 + (i0 - 1) + bmod_u;
+  }
+  constexpr int SB = Stage<T, KT>::bytes;
+  static_assert(kStages == 4, "the march below is unrolled over a ring of 4 stages");
+  const unsigned char* cbase_u = reinterpret_cast<const unsigned char*>(u);
+  const unsigned char* cbase_k = reinterpret_cast<const unsigned char*>(k);
+  const int lane_u = (kTJ * h * RowGeom<T>::stride + l) * (int)sizeof(T);  // row 4h, column l
+  const int lane_k = Stage<T, KT>::u_bytes + (kTJ * h * RowGeom<KT>::stride + l) * (int)sizeof(KT);
+  const unsigned char* ring_u = ring + lane_u;
+  const unsigned char* ring_k = ring + lane_k;
+  const int dk = bmod_k - bmod_u;
+  // stage plane ch.q into stage st if the march needs it; one group per plane
+  auto issue_next = [&](int st) {
+    issue_plane<T, KT>(ring_s + st * SB, ch, cl, N, j0 - 1, lim, bmod_u, bmod_k, cbase_u, cbase_k, ch.q <= qend);
+    cp_async_commit();
+    ch.next(N, j0 - 1);
+  };
+  auto read_next = [&](Plane<T>& P, int st) {
+    const int pl = rh.q;
+    read_plane<T, KT>(P, ring_u + st * SB, ring_k + st * SB, rh, 0, dk);
+    if (MODE == OP_RESID || MODE == OP_JACOBI || MODE == OP_CHEB) {
+      // f (and d_in) at the lane's nodes of this plane, needed one step later
+      const int lim_r = N - 1 - i - jb - pl;
+#pragma unroll
+      for (int r = 0; r < kTJ; ++r) {
+        const bool ok = r <= lim_r && pl >= k0;
+        P.fv[r] = ok ? __ldg(static_cast<const T*>(q.f) + P.off[r]) : (T)0;
+        if (MODE == OP_CHEB) P.dv[r] = ok && q.ca != 0.0 ? __ldg(static_cast<const T*>(q.d_in) + P.off[r]) : (T)0;
+      }
+    }
+    rh.next(N, jb - 1);
+  };
+  // planes k0-1 .. k0+1 into stages 0..2; the step for plane k0+t (t mod 4)
+  // then copies plane k0+t+2 into stage (3+t) mod 4 and reads stage (1+t) mod 4
+  issue_next(0);
+  issue_next(1);
+  issue_next(2);
+  cp_async_wait<kStages - 2>();
+  __syncwarp();
+  Plane<T> X, Y;
+  read_next(X, 0);  // plane k0-1
+  Acc<T, DIAG> yX[kTJ], yY[kTJ];
+  auto store = [&](const Plane<T>& P, Acc<T, DIAG>(&y)[kTJ], int pl) {
+    const int lim_r = N - 1 - i - jb - pl;  // row r holds a volume node iff r <= lim_r
+#pragma unroll
+    for (int r = 0; r < kTJ; ++r)
+      if (r <= lim_r) finish_node<T, MODE>(y[r].y, y[r].d, P.c0[r + 1].x, P.off[r], q, P.fv[r], P.dv[r]);
+  };
+  auto step = [&](auto tc, Plane<T>& P, Plane<T>& Q, Acc<T, DIAG>(&yP)[kTJ], Acc<T, DIAG>(&yQ)[kTJ], int qq) {
+    constexpr int t = decltype(tc)::value;
+    __syncwarp();                  // every lane has read plane qq-2 before its stage is refilled
+    issue_next((3 + t) & 3);       // plane qq + 2
+    cp_async_wait<kStages - 2>();  // this lane's copies of plane qq have landed
+    __syncwarp();                  // ... and every other lane's
+    read_next(Q, (1 + t) & 3);     // plane qq
+    step_edges<T, DIAG>(P, Q, c, yP, yQ);
+    if (t != 0 || qq - 1 >= k0) store(P, yP, qq - 1);
+  };
+  for (int qq = k0; qq <= qend; qq += 4) {
+    step(std::integral_constant<int, 0>{}, X, Y, yX, yY, qq);
+    if (qq + 1 > qend) break;
+    step(std::integral_constant<int, 1>{}, Y, X, yY, yX, qq + 1);
+    if (qq + 2 > qend) break;
+    step(std::integral_constant<int, 2>{}, X, Y, yX, yY, qq + 2);
+    if (qq + 3 > qend) break;
+    step(std::integral_constant<int, 3>{}, Y, X, yY, yX, qq + 3);
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+// Partial row of one stored copy (its tet's micro-elements only).  Neighbour
+// offsets: plane starts P(k) and row starts within planes k-1, k, k+1 are
+// formed once; the 14 directions then only add constants.
+template <class T, class KT>
+__device__ __forceinline__ void scaled_partial(const DepthDev& D, const T* __restrict__ sten, const BCopy& cp,
+                                               const T* __restrict__ u, const KT* __restrict__ k, T& y, T& diag) {
+  const TetDev td = D.tets[cp.slot];
+  const int N = td.N;
+  const T* st = sten + (cp.slot * 16 + cp.mask) * kNDir;
+  const T* ut = u + td.base;
+  const KT* kt = k + td.base;
+  const int ci = cp.i, cj = cp.j, ck = cp.k;
+  // plane start of plane kk and start of row jj in it
+  auto pstart = [&](int kk) { return (int)(tetnum(N + 1) - tetnum(N + 1 - kk)); };
+  auto rstart = [&](int pk, int kk, int jj) { return pk + jj * (N - kk + 1) - jj * (jj - 1) / 2; };
+  const int p0 = pstart(ck);
+  const int pm = ck > 0 ? pstart(ck - 1) : 0;
+  const int pp = ck < N ? pstart(ck + 1) : 0;
+  const int x = rstart(p0, ck, cj) + ci;
+  const T ux = ut[x];
+  const T kx = (T)ldk(kt, x);
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) {
+    int di, dj, dk;
+    dir_of(d, di, dj, dk);
+    const int a = ci + di, b = cj + dj, cc = ck + dk;
+    if (a < 0 || b < 0 || cc < 0 || a + b + cc > N) continue;
+    const int ps = dk == 0 ? p0 : (dk < 0 ? pm : pp);
+    const int idx = rstart(ps, cc, b) + a;
+    const T sv = st[d] * (kx + (T)ldk(kt, idx));
+    y = fma(sv, ut[idx] - ux, y);
+    diag -= sv;
+  }
+}
+
+template <class T, class KT, int MODE>
+__device__ void boundary_node(const DepthDev& D, const T* __restrict__ sten, int b, const OpPtrs& p) {
+  const int lo = D.bstart[b], hi = D.bstart[b + 1];
+  T* out = static_cast<T*>(p.out);
+  if (D.bdir[b]) {
+    for (int q = lo; q < hi; ++q) {
+      const long long idx = D.bcopies[q].idx;
+      out[idx] = MODE == OP_DIAG ? (T)1 : (T)0;
+      if (MODE == OP_CHEB) static_cast<T*>(p.d_out)[idx] = 0;
+    }
+    return;
+  }
+  const T* u = static_cast<const T*>(p.u);
+  const KT* k = static_cast<const KT*>(p.k);
+  T y = 0, diag = 0;
+  for (int q = lo; q < hi; ++q) {
+    const BCopy cp = D.bcopies[q];
+    scaled_partial<T, KT>(D, sten, cp, u, k, y, diag);
+  }
+  const long long i0 = D.bcopies[lo].idx;
+  const T ux = u[i0];
+  T val = y, dval = 0;
+  if (MODE == OP_RESID) {
+    val = __ldg(static_cast<const T*>(p.f) + i0) - y;
+  } else if (MODE == OP_JACOBI) {
+    val = ux + sdiv((T)p.omega * (__ldg(static_cast<const T*>(p.f) + i0) - y), diag);
+  } else if (MODE == OP_CHEB) {
+    const T prev = p.ca != 0.0 ? (T)p.ca * __ldg(static_cast<const T*>(p.d_in) + i0) : (T)0;
+    dval = prev + (T)p.cb * (__ldg(static_cast<const T*>(p.f) + i0) - y) / diag;
+    val = ux + dval;
+  } else if (MODE == OP_DIAG) {
+    val = diag;
+  }
+  for (int q = lo; q < hi; ++q) {
+    const long long idx = D.bcopies[q].idx;
+    out[idx] = val;
+    if (MODE == OP_CHEB) static_cast<T*>(p.d_out)[idx] = dval;
+  }
+}
+
+// Persistent kernel: warps take volume items (longest first), then chunks of
+// 32 interface nodes.  Dynamic shared memory: one staging ring per warp.
+template <class T, class KT, int MODE>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 2 : 4) scaled_op_kernel(DepthDev D, OpPtrs p, int n_items, int n_bnodes,
+                                                            unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  (void)err;
+  const T* sten = nullptr;
+  if constexpr (sizeof(T) == 8)
+    sten = reinterpret_cast<const T*>(D.sten64);
+  else
+    sten = reinterpret_cast<const T*>(D.sten32);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned char* ring = smem_raw + wib * Stage<T, KT>::warp_bytes;
+  const unsigned ring_s = smem_addr(ring);
+  const CopyLane cl = copy_lane<T, KT>(lane);
+  // Work in quads of 4 positions (one per warp of a block): volume quads
+  // (4 consecutive items: the work list groups j-stacked tiles in fours) and
+  // interface quads (4 chunks of 32 nodes) spread evenly among them.
+  const int nchunks = (n_bnodes + 31) / 32;
+  const int vq = (n_items + 3) / 4, bq = (nchunks + 3) / 4;
+  const int totq = vq + bq;
+  const int R = bq ? max(1, totq / bq) : totq + 1;
+  for (int it = warp; it < 4 * totq; it += nwarps) {
+    const int qd = it >> 2, sub = it & 3;
+    const int before = min(bq, qd / R);  // interface quads before this one
+    if (qd % R == R - 1 && qd / R < bq) {
+      const int b = ((qd / R) * 4 + sub) * 32 + lane;
+      if (b < n_bnodes) boundary_node<T, KT, MODE>(D, sten, b, p);
+    } else {
+      const int v = (qd - before) * 4 + sub;
+      if (v < n_items) volume_item<T, KT, MODE>(D, sten, D.items[v], lane, p, ring, ring_s, cl);
+    }
+  }
+}
+
+// Interface rows on their own: one thread per unique boundary node, launched
+// on the mesh's side stream ahead of the volume kernel (its blocks take the
+// SMs first and the persistent volume blocks start as they drain), instead
+// of as chunks inside the volume kernel's loop.
+template <class T, class KT, int MODE>
+__global__ void __launch_bounds__(128) boundary_only_kernel(DepthDev D, OpPtrs p, int n_b) {
+  const T* sten;
+  if constexpr (sizeof(T) == 8)
+    sten = reinterpret_cast<const T*>(D.sten64);
+  else
+    sten = reinterpret_cast<const T*>(D.sten32);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_b; b += gridDim.x * blockDim.x)
+    boundary_node<T, KT, MODE>(D, sten, b, p);
+}
+
+template <class T, class KT>
+constexpr int ring_bytes() {
+  return 4 * Stage<T, KT>::warp_bytes;  // 4 warps per block
+}
+
+template <class T, class KT, int MODE>
+static int occupancy() {
+  static int occ = 0;
+  if (!occ) {
+    HHG_CUDA(cudaFuncSetAttribute(scaled_op_kernel<T, KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ring_bytes<T, KT>()));
+    HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, scaled_op_kernel<T, KT, MODE>, 128,
+                                                           ring_bytes<T, KT>()));
+    if (occ < 1) occ = 1;
+  }
+  return occ;
+}
+
+template <class T, class KT>
+static void init_typed() {
+  occupancy<T, KT, OP_APPLY>();
+  occupancy<T, KT, OP_RESID>();
+  occupancy<T, KT, OP_JACOBI>();
+  occupancy<T, KT, OP_CHEB>();
+  occupancy<T, KT, OP_DIAG>();
+}
+
+// Launch configurations are computed once, outside any stream capture.
+void init_launch_configs(int dtype) {
+  if (dtype == HHG_F64 || dtype == kF64KBF16)
+    init_typed<double, double>();
+  else if (dtype == HHG_F32)
+    init_typed<float, float>();
+  else
+    init_typed<float, __nv_bfloat16>();
+}
+
+template <class T, class KT, int MODE>
+static void launch_typed(const Mesh& m, int depth, const OpArgs& a, const void* kptr, cudaStream_t s) {
+  const Depth& Dh = m.depth[depth];
+  const DepthDev& D = Dh.dev;
+  const int n_items = a.nc_only ? D.n_items_nc : D.n_items;
+  const int n_b = a.nc_only ? D.n_bnodes_nc : D.n_bnodes;
+  const int work = n_items + (n_b + 31) / 32;
+  if (work == 0) return;
+  const int occ = occupancy<T, KT, MODE>();
+  OpPtrs p{a.u, kptr, a.f, a.out, a.d_in, a.d_out, a.omega, a.ca, a.cb};
+  if (n_items > 0 && n_b > 0 && m.side) {
+    // fork: interface rows on the side stream, volume rows here; join before
+    // returning (also valid inside a stream capture)
+    HHG_CUDA(cudaEventRecord(m.side_fork, s));
+    HHG_CUDA(cudaStreamWaitEvent(m.side, m.side_fork, 0));
+    boundary_only_kernel<T, KT, MODE><<<(n_b + 127) / 128, 128, 0, m.side>>>(D, p, n_b);
+    HHG_CUDA(cudaGetLastError());
+    HHG_CUDA(cudaEventRecord(m.side_join, m.side));
+    const int blocks = std::min((n_items + 3) / 4, m.num_sms * occ);
+    scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, 0, m.d_error);
+    HHG_CUDA(cudaGetLastError());
+    HHG_CUDA(cudaStreamWaitEvent(s, m.side_join, 0));
+    return;
+  }
+  const int blocks = std::min((work + 3) / 4, m.num_sms * occ);
+  scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, n_b, m.d_error);
+  HHG_CUDA(cudaGetLastError());
+}
+
+template <int MODE>
+static void launch_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, cudaStream_t s) {
+  const Depth& Dh = m.depth[depth];
+  if (dtype == HHG_F64)
+    launch_typed<double, double, MODE>(m, depth, a, Dh.k64, s);
+  else if (dtype == kF64KBF16)
+    launch_typed<double, double, MODE>(m, depth, a, Dh.k16d, s);
+  else if (dtype == HHG_F32)
+    launch_typed<float, float, MODE>(m, depth, a, Dh.k32, s);
+  else
+    launch_typed<float, __nv_bfloat16, MODE>(m, depth, a, Dh.k16, s);
+}
+
+void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case OP_APPLY: launch_mode<OP_APPLY>(m, depth, dtype, a, s); break;
+    case OP_RESID: launch_mode<OP_RESID>(m, depth, dtype, a, s); break;
+    case OP_JACOBI: launch_mode<OP_JACOBI>(m, depth, dtype, a, s); break;
+    case OP_CHEB: launch_mode<OP_CHEB>(m, depth, dtype, a, s); break;
+    case OP_DIAG: launch_mode<OP_DIAG>(m, depth, dtype, a, s); break;
   }
 }
 

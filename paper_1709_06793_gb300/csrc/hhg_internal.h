@@ -92,28 +92,7 @@ struct DepthDev {
   int n_vf_nc;
   const int* fslot;            // slot of the same tet at depth-1 (-1 at depth 0)
   const unsigned char* mult;   // [slot][16] copies of a node of that face mask
-  // scaled operator (scaled.cu): tiles of two macro tets of equal level
-  // (x = slotA<<20 | j0<<10 | i0, y = k0, z = k1, w = slotB | kPairSingle if
-  // slotA has no partner), the Dirichlet status of every face mask per slot
-  // (bit m: nodes of mask m are Dirichlet), the interface and Dirichlet
-  // copies the tile kernel does not write (mask | kCopyDirichlet), and the
-  // unique non-Dirichlet interface nodes (indices into bstart) whose copies
-  // are summed
-  const int4* pitems;
-  int n_pitems;
-  int n_pitems_nc;
-  const unsigned short* dmask;
-  const BCopy* fcopies;
-  int n_fcopies;
-  int n_fcopies_nc;
-  const int* isum;
-  int n_isum;
-  int n_isum_nc;
-  const int* sstart;  // copies of isum[t]: sidx[sstart[t] .. sstart[t+1]) (stored indices)
-  const int* sidx;
 };
-constexpr int kPairSingle = 1 << 30;
-constexpr short kCopyDirichlet = 0x10;
 
 // Host-side description of one depth.
 struct Depth {
@@ -141,17 +120,6 @@ struct Depth {
   int n_vf = 0, n_vf_nc = 0;
   std::vector<int> h_fslot;
   std::vector<unsigned char> h_mult;
-  std::vector<int4> h_pitems;
-  int n_pitems = 0, n_pitems_nc = 0;
-  std::vector<unsigned short> h_dmask;
-  std::vector<BCopy> h_fcopies;
-  int n_fcopies = 0, n_fcopies_nc = 0;
-  std::vector<int> h_isum, h_sstart, h_sidx;
-  int n_isum = 0, n_isum_nc = 0;
-  // summed diagonal of every unique non-Dirichlet interface node (h_isum
-  // order) per dtype (FP64, FP32, FP32 with bfloat16 k, FP64 with bfloat16
-  // k), set with the coefficient
-  void* dsum[4] = {nullptr, nullptr, nullptr, nullptr};
   DepthDev dev{};
   // device allocations owned by this depth
   std::vector<void*> allocations;
@@ -286,13 +254,6 @@ void elements_for(const Mesh& m, int tet, int level, double* out6x16);
 void* dalloc(Depth& d, size_t bytes);
 void build_items(const Mesh& m, Depth& D);
 void set_kseg(Mesh& m, int kseg, int korder);
-// scaled operator work lists (scaled.cu): tile pairs, copy lists, Dirichlet masks
-void build_scaled_lists(const Mesh& m, Depth& D);
-void build_pair_items(const Mesh& m, Depth& D);
-void upload_scaled_lists(Depth& D);
-void upload_pair_items(Depth& D);
-// summed interface diagonals of every depth and dtype (after the coefficient changed)
-void compute_interface_diagonals(Mesh& m, cudaStream_t s);
 
 // ---- kernels (apply.cu / mg.cu) ----------------------------------------------
 enum OpMode { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_CHEB = 3, OP_DIAG = 4 };

@@ -558,7 +558,6 @@ static void build_depth(Mesh& m, int d) {
       const BCopy& c = D.h_bcopies[q];
       D.h_mult[(size_t)c.slot * 16 + c.mask] = (unsigned char)(D.h_bstart[b + 1] - D.h_bstart[b]);
     }
-  build_scaled_lists(m, D);
 }
 
 template <class T>
@@ -578,13 +577,11 @@ void set_kseg(Mesh& m, int kseg, int korder) {
   m.korder = korder;
   for (Depth& D : m.depth) {
     build_items(m, D);
-    build_pair_items(m, D);
     if (m.device) {
       HHG_CUDA(cudaDeviceSynchronize());
       D.dev.items = reupload(D, const_cast<int4*>(D.dev.items), D.h_items);
       D.dev.n_items = D.n_items;
       D.dev.n_items_nc = D.n_items_nc;
-      upload_pair_items(D);
     }
   }
 }
@@ -621,7 +618,6 @@ static void upload_depth(Depth& D) {
   D.dev.n_stored_nc = D.n_stored_nc;
   D.dev.fslot = upload(D, D.h_fslot);
   D.dev.mult = upload(D, D.h_mult);
-  upload_scaled_lists(D);
 }
 
 // Unknowns of every component at the depth where it reaches the coarsest level.
