@@ -65,7 +65,7 @@ typedef enum {
     HHG_ERR_CUDA = -2,          /* a CUDA runtime call failed */
     HHG_ERR_NOMEM = -3,         /* device or host allocation failed */
     HHG_ERR_NOT_CONVERGED = -4, /* solver hit its iteration limit */
-    HHG_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+    HHG_ERR_TIMEOUT = -5,       /* reserved for a bounded device wait running out (no kernel waits today) */
     HHG_ERR_STATE = -6          /* call order violated (e.g. no coefficient set) */
 } hhg_status;
 
@@ -190,7 +190,9 @@ int hhg_get_stencils(hhg_mesh mesh, int tet, int depth, double* out);
  * layout, positive and equal on all copies of a node.  The library keeps
  * its own FP64, FP32 and BF16 copies and injects them to every depth
  * (coarse nodal value = fine nodal value at the same point).  Must precede
- * any operator call.  Stream-ordered; allocates on first call. */
+ * any operator call.  Allocates on first call.  Every entry is checked on the
+ * device first: HHG_ERR_ARG (and nothing changed) if one is NaN, infinite,
+ * zero or negative; the check synchronises `stream`. */
 int hhg_set_coefficient(hhg_mesh mesh, const double* k_dev, void* stream);
 
 /* y = A_s(k) u: the scaled operator (Sec. 6.1) at `depth` on all active tets.
@@ -353,10 +355,11 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
 int hhg_set_option(hhg_mesh mesh, const char* key, double value);
 int hhg_get_option(hhg_mesh mesh, const char* key, double* value);
 
-/* Device-side error check: HHG_ERR_TIMEOUT if a kernel of this mesh hit the
- * iteration limit of one of its bounded waits since the last check (the
- * results of that call are invalid), HHG_OK otherwise.  Synchronous; clears
- * the flag. */
+/* Device-side error word of the mesh: HHG_ERR_TIMEOUT if a kernel had set it
+ * since the last check, HHG_OK otherwise.  No kernel of this library waits on
+ * memory written by another block or launch (the staging waits are cp.async
+ * groups), so none sets it and the call returns HHG_OK; it is kept for kernels
+ * with bounded waits.  Synchronous; clears the word. */
 int hhg_device_status(hhg_mesh mesh);
 
 /* Message of the last failed call on this thread ("" if none). */

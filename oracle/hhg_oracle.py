@@ -21,10 +21,12 @@ It computes, from the paper's definitions and nothing else,
 * global assembly over unique nodes (nodes on macro faces/edges/vertices are
   shared by all macro tetrahedra that contain them, Sec. 2.1), homogeneous
   Dirichlet rows removed (Sec. 2);
-* geometric multigrid by the readings listed in the design notes: linear
-  interpolation P, R = P^T, re-discretised coarse operators, damped Jacobi and
-  Chebyshev smoothers, dense Cholesky on the coarsest level, symmetric V-cycle
-  and preconditioned CG (the paper fixes only the V(3,3) cycle, Sec. 7.2).
+* geometric multigrid (the paper fixes only the V(3,3) cycle, Sec. 7.2; these
+  are readings where it is silent): linear interpolation P (exact for nested
+  P1 spaces), R = P^T, coarse operators re-discretised with the same scaled
+  rule and k sampled at the coarse nodes, damped Jacobi (omega = 2/3) and
+  degree-2 Chebyshev smoothers, dense Cholesky on the coarsest level, a
+  symmetric V-cycle and CG preconditioned by one V-cycle from a zero guess.
 
 Nothing here shares code with the CUDA path.  Vectors are indexed by unique
 node (see LevelMesh), never by the CUDA path's stored layout.
@@ -682,7 +684,8 @@ class Hierarchy:
 
 
 # ----------------------------------------------------------------------------
-# Error norms (Sec. 7.2: discrete L2; readings in the design notes)
+# Error norms (Sec. 7.2 asks for an appropriately scaled nodal L2 error without
+# fixing it: read as sqrt(e^T M_L e) with the lumped P1 mass; H1 by quadrature)
 # ----------------------------------------------------------------------------
 
 

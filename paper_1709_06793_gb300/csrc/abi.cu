@@ -216,8 +216,7 @@ int hhg_apply_tensor(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, i
     if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
     const int pr = dtype == HHG_F64 ? 0 : 1;
     OpArgs a{u_dev, nullptr, y_dev, nullptr, nullptr, 0, 0, 0, 0};
-    launch_tensor_op(m, depth, dtype, OP_APPLY, a, workspace(m, depth, pr, 12), workspace(m, depth, pr, 13),
-                     (cudaStream_t)stream);
+    launch_tensor_op(m, depth, dtype, OP_APPLY, a, (cudaStream_t)stream);
   });
 }
 

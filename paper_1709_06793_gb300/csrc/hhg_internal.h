@@ -143,7 +143,6 @@ struct Depth {
   // slots: 0 F (depth>0) / CG r (depth 0), 1 U / CG z, 2 V-cycle residual,
   // 3 CG p, 4 smoother ping-pong, 5-6 Chebyshev updates, 7 CG q, 8 inner solution
   // 9 inner solution, 10 operator scratch (nodal modes), 11 spare
-  // 12-13 tensor-operator partial rows and diagonals
   void* ws[2][14] = {{nullptr}};
   void* ndinv[4] = {nullptr, nullptr, nullptr, nullptr};  // nodal operator 1/diag per dtype (0 on Dirichlet)
   int* cslot_map = nullptr;  // slot at depth+1 of each slot (prolongation)
@@ -277,9 +276,9 @@ void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void
 void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 // nodal-integration operator in the modes above (dinv: 1/diag, 0 on Dirichlet nodes; tmp: a scratch vector)
 void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s);
-// scaled operator of the tensor coefficient (M = 6) in the modes above (py, pd: scratch vectors)
+// scaled operator of the tensor coefficient (M = 6) in the modes above
 void compute_tensor_weights(Mesh& m, cudaStream_t s);
-void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, void* py, void* pd,
+void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a,
                       cudaStream_t s);
 void ensure_tensor_stencils(Mesh& m);
 void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, const void* dinv, void* tmp,

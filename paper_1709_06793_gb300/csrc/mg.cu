@@ -119,7 +119,31 @@ void set_tensor_coefficient(Mesh& m, const double* K6, cudaStream_t s) {
   for (int t = 0; t < 4; ++t) m.cinv_ready[3][t] = false;
 }
 
+// Flags a coefficient that is not finite and positive at some stored node
+// (the scaled rule of eq. "discrete" needs k > 0 for a positive operator).
+__global__ void check_k_kernel(const double* __restrict__ k, long long n, unsigned* bad) {
+  unsigned b = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = k[i];
+    if (!(v > 0.0) || !isfinite(v)) b = 1;  // NaN fails v > 0
+  }
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
 void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
+  {
+    unsigned* bad = m.d_counter + 48;
+    HHG_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
+    const long long n = m.depth[0].n_stored;
+    if (n > 0) {
+      check_k_kernel<<<grid_for(n, 256, 8 * std::max(m.num_sms, 1)), 256, 0, s>>>(k, n, bad);
+      HHG_CUDA(cudaGetLastError());
+    }
+    unsigned hb = 0;
+    HHG_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HHG_CUDA(cudaStreamSynchronize(s));
+    HHG_REQUIRE(hb == 0, "hhg_set_coefficient: k must be finite and positive at every stored node");
+  }
   drop_graphs(m);
   learned_invalidate(m);
   for (int d = 0; d < m.ndepth; ++d) {
@@ -667,8 +691,7 @@ static void op(Mesh& m, int depth, int dtype, OpMode mode, const void* u, const 
                void* dout, double omega, double ca, double cb, bool nc_only, cudaStream_t s) {
   OpArgs a{u, f, out, din, dout, omega, ca, cb, nc_only ? 1 : 0};
   if (m.opk == 3)
-    launch_tensor_op(m, depth, dtype, mode, a, workspace(m, depth, prec_of(dtype), 12),
-                     workspace(m, depth, prec_of(dtype), 13), s);
+    launch_tensor_op(m, depth, dtype, mode, a, s);
   else if (m.opk == 1)
     launch_volface_op(m, depth, dtype, mode, a, s);
   else if (m.opk == 2)

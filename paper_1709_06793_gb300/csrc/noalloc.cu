@@ -15,6 +15,7 @@
 // the device symbol, not a device address); it looks the device address up
 // once per device with cudaGetSymbolAddress and passes that pointer.
 #include <mutex>
+#include <new>
 
 #include "hhg_internal.h"
 
@@ -96,6 +97,9 @@ extern "C" int hhg_smooth_noalloc(hhg_mesh mesh, int depth, int sweeps, double o
   } catch (const Error& e) {
     set_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return HHG_ERR_NOMEM;
   } catch (const std::exception& e) {
     set_error(e.what());
     return HHG_ERR_ARG;

@@ -178,7 +178,7 @@ __global__ void tensor_bnodes_kernel(DepthDev D, const T* __restrict__ tsten, co
 }
 
 template <class T, int MODE>
-static void tensor_typed(const Mesh& m, int depth, const OpArgs& a, void* py, void* pd, cudaStream_t s) {
+static void tensor_typed(const Mesh& m, int depth, const OpArgs& a, cudaStream_t s) {
   const Depth& Dh = m.depth[depth];
   const DepthDev& D = Dh.dev;
   const int n_rows = a.nc_only ? D.n_rows_nc : D.n_rows;
@@ -196,8 +196,6 @@ static void tensor_typed(const Mesh& m, int depth, const OpArgs& a, void* py, vo
     tb = Dh.tb32;
   }
   TensorPtrs p{a.u, a.f, a.out, a.omega};
-  (void)py;
-  (void)pd;
   if (n_rows > 0) {
     const int g = std::max(1, std::min((n_rows + 7) / 8, 16 * m.num_sms));
     tensor_volume_kernel<T, MODE><<<g, 256, 0, s>>>(D, tb, D.n_stored, p, n_rows);
@@ -210,25 +208,25 @@ static void tensor_typed(const Mesh& m, int depth, const OpArgs& a, void* py, vo
 }
 
 template <class T>
-static void tensor_dispatch(const Mesh& m, int depth, OpMode mode, const OpArgs& a, void* py, void* pd,
+static void tensor_dispatch(const Mesh& m, int depth, OpMode mode, const OpArgs& a,
                             cudaStream_t s) {
   switch (mode) {
-    case OP_APPLY: tensor_typed<T, OP_APPLY>(m, depth, a, py, pd, s); break;
-    case OP_RESID: tensor_typed<T, OP_RESID>(m, depth, a, py, pd, s); break;
-    case OP_JACOBI: tensor_typed<T, OP_JACOBI>(m, depth, a, py, pd, s); break;
-    case OP_DIAG: tensor_typed<T, OP_DIAG>(m, depth, a, py, pd, s); break;
+    case OP_APPLY: tensor_typed<T, OP_APPLY>(m, depth, a, s); break;
+    case OP_RESID: tensor_typed<T, OP_RESID>(m, depth, a, s); break;
+    case OP_JACOBI: tensor_typed<T, OP_JACOBI>(m, depth, a, s); break;
+    case OP_DIAG: tensor_typed<T, OP_DIAG>(m, depth, a, s); break;
     default: throw Error{HHG_ERR_ARG, "the tensor operator has no Chebyshev mode"};
   }
 }
 
-void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, void* py, void* pd,
+void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a,
                       cudaStream_t s) {
   HHG_REQUIRE(m.tensor_set, "hhg_set_tensor_coefficient must be called first");
   HHG_REQUIRE(dtype == HHG_F64 || dtype == HHG_F32, "the tensor operator runs in HHG_F64 or HHG_F32");
   if (dtype == HHG_F64)
-    tensor_dispatch<double>(m, depth, mode, a, py, pd, s);
+    tensor_dispatch<double>(m, depth, mode, a, s);
   else
-    tensor_dispatch<float>(m, depth, mode, a, py, pd, s);
+    tensor_dispatch<float>(m, depth, mode, a, s);
 }
 
 }  // namespace hhg

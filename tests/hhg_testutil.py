@@ -78,3 +78,48 @@ def lattice_field(X, scale):
     h = h * np.int64(-4658895280553007687)
     v = ((h >> 20) & np.int64((1 << 40) - 1)).astype(np.float64) / float(1 << 40)
     return 2.0 * v - 1.0
+
+
+def sampled_residuals(O, H, m, V, T, level, x_dev, f_dev, kfun, n_vol, n_face, seed):
+    """FP64 residuals f_i - (A x)_i at sampled stored rows of a single-level
+    mesh, each row evaluated by the oracle's one-row evaluator (row_apply)
+    from the solution's values at the row's neighbours (gathered from the
+    device vector) and the exact coefficient kfun(X).  Returns (sampled stored
+    indices, oracle residuals).  Dirichlet rows are not sampled."""
+    import torch
+
+    off, lev, n = m.layout(0)
+    nodes = stored_nodes(off, lev)
+    N = 1 << level
+    t_, i_, j_, k_ = nodes.T
+    face = (i_ == 0) | (j_ == 0) | (k_ == 0) | (i_ + j_ + k_ == N)
+    mm = O.MacroMesh(V, T)
+    Tn = np.asarray(T)
+    tet_of = {tuple(int(v) for v in Tn[t]): t for t in range(len(Tn))}
+    rng = np.random.default_rng(seed)
+    cand_v = np.nonzero(~face)[0]
+    cand_f = np.nonzero(face)[0]
+    pick_f = []
+    for q in rng.permutation(cand_f):  # face rows that are not Dirichlet
+        t, i, j, kk = nodes[q]
+        Wt = np.array([N - i - j - kk, i, j, kk])
+        if not mm.on_boundary(Tn[t][Wt > 0]):
+            pick_f.append(q)
+        if len(pick_f) == n_face:
+            break
+    sample = np.concatenate([rng.choice(cand_v, n_vol, replace=False), np.array(pick_f, dtype=np.int64)])
+
+    def field_u(gv, W, X):
+        t = tet_of[tuple(int(v) for v in gv[0])]
+        idx = node_index(off, np.full(len(W), t), W[:, 1], W[:, 2], W[:, 3], N)
+        return x_dev[torch.as_tensor(idx, device=x_dev.device)].double().cpu().numpy()
+
+    def field_k(gv, W, X):
+        return kfun(X)
+
+    fs = f_dev[torch.as_tensor(sample, device=f_dev.device)].double().cpu().numpy()
+    r = np.empty(len(sample))
+    for q, (t, i, j, kk) in enumerate(nodes[sample]):
+        Wt = np.array([N - i - j - kk, i, j, kk])
+        r[q] = fs[q] - O.row_apply(mm, level, Tn[t][Wt > 0], Wt[Wt > 0], field_u, field_k, "scaled")
+    return sample, r

@@ -114,8 +114,11 @@ def test_48_random_tets_mixed_levels_fp32_apply_sampled(H):
 
 def test_level7_mixed_solve_residual_full_size(H):
     """FP32 GMG-CG with FP64 refinement on the 2.2 M-node level-7 cube: the
-    FP64 residual of the returned solution, computed here with the FP64
-    operator and dot, is within the requested tolerance."""
+    returned solution's FP64 residual, evaluated row by row by the oracle at
+    sampled volume and interface rows, meets the requested 1e-8 (every row of
+    the residual is bounded by its 2-norm over the unique unknowns, computed
+    here from f on the host), and the library's own FP64 residual agrees with
+    the oracle's at those rows."""
     V, T = I.kuhn_cube()
     m = H.Mesh(V, T, 7, 2)
     off, lev, n = m.layout(0)
@@ -126,10 +129,19 @@ def test_level7_mixed_solve_residual_full_size(H):
     H.hhg_apply_mass(m.h, 0, fi, f, H.HHG_F64)
     u = torch.zeros(n, device="cuda", dtype=torch.float64)
     st = H.hhg_solve(m.h, f, u, tol=1e-8, mode=H.HHG_SOLVE_MIXED)
+    assert st["rel_residual"] <= 1e-8
+    # ||f||_2 over unique unknowns: one entry per node key
+    nodes = U.stored_nodes(off, lev)
+    keys = U.stored_keys(T, nodes, lev)
+    _, first = np.unique(keys, return_index=True)
+    fh = f.cpu().numpy()
+    nf = float(np.sqrt(np.sum(fh[first] ** 2)))
+    sample, r_or = U.sampled_residuals(O, H, m, V, T, 7, u, f, I.k_cube, 300, 100, seed=21)
+    assert np.max(np.abs(r_or)) <= 1e-8 * nf, (np.max(np.abs(r_or)), nf)
     r = torch.empty_like(u)
     H.hhg_residual(m.h, 0, f, u, r, H.HHG_F64)
-    rel = (H.hhg_dot(m.h, 0, r, r, H.HHG_F64) / H.hhg_dot(m.h, 0, f, f, H.HHG_F64)) ** 0.5
-    assert rel <= 1e-8 and abs(rel - st["rel_residual"]) <= 1e-3 * max(rel, 1e-16)
+    r_lib = r[torch.as_tensor(sample, device="cuda")].cpu().numpy()
+    assert np.max(np.abs(r_lib - r_or)) <= 1e-12 * float(np.max(np.abs(fh))), np.max(np.abs(r_lib - r_or))
     m.close()
 
 

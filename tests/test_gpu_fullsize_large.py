@@ -146,6 +146,11 @@ def test_large_bf16k_apply_sampled(big):
 
 
 def test_large_bf16k_mixed_solve_residual(big):
+    """BF16-k mixed solve at full size: the oracle's FP64 residual of the
+    returned solution at sampled volume and interface rows (the coefficient
+    is the bfloat16-rounded k the library was given) is within the requested
+    1e-8 of ||f||_2 (bounded above here by the 2-norm over all stored copies),
+    and the library's FP64 residual agrees with it at those rows."""
     H, m, V, T, off, lev, n, u = big
     ones = torch.ones(n, device="cuda", dtype=torch.float64)
     f = torch.empty_like(ones)
@@ -153,8 +158,12 @@ def test_large_bf16k_mixed_solve_residual(big):
     del ones
     x = torch.zeros_like(f)
     st = H.hhg_solve(m.h, f, x, tol=1e-8, mode=H.HHG_SOLVE_MIXED_KBF16)
+    assert st["rel_residual"] <= 1e-8, st
+    nf_upper = float(torch.sqrt(torch.sum(f * f)))
+    sample, r_or = U.sampled_residuals(O, H, m, V, T, LEVEL, x, f, _k_field, 200, 100, seed=31)
+    assert np.max(np.abs(r_or)) <= 1e-8 * nf_upper, (np.max(np.abs(r_or)), nf_upper)
     r = torch.empty_like(x)
     H.hhg_residual(m.h, 0, f, x, r, H.HHG_F64)
-    rel = (H.hhg_dot(m.h, 0, r, r, H.HHG_F64) / H.hhg_dot(m.h, 0, f, f, H.HHG_F64)) ** 0.5
-    assert rel <= 1e-8, (rel, st)
-    assert abs(rel - st["rel_residual"]) <= 1e-3 * max(rel, 1e-16)
+    r_lib = r[torch.as_tensor(sample, device="cuda")].cpu().numpy()
+    fmax = float(torch.max(torch.abs(f)))
+    assert np.max(np.abs(r_lib - r_or)) <= 1e-12 * fmax, np.max(np.abs(r_lib - r_or))

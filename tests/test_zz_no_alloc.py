@@ -28,14 +28,14 @@ def H():
     return hhg
 
 
-@pytest.mark.parametrize("dtype,tol", [(0, 1e-12), (1, 1e-6)])
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-12), (1, 1e-6), (2, 1e-6)])
 def test_noalloc_matches_smooth_on_two_calls(H, dtype, tol):
     V, T = I.kuhn_cube()
     m = H.Mesh(V, T, 5, 2)
     off, lev, n = m.layout(0)
     xyz = m.coords(0)
     H.hhg_set_coefficient(m.h, torch.tensor(I.k_cube(xyz), device="cuda"))
-    tdt = torch.float64 if dtype == 0 else torch.float32
+    tdt = torch.float64 if dtype == 0 else torch.float32  # dtype 2: FP32 vectors, bfloat16 k
     x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]  # smooth fields: equal on every copy of a node
     f = torch.tensor(np.sin(2 * x + y) * np.cos(z), device="cuda", dtype=tdt)
     u0 = torch.tensor(np.cos(3 * x - 2 * y + z), device="cuda", dtype=tdt)
