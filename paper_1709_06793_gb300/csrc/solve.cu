@@ -329,7 +329,12 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
       HHG_CUDA(cudaGetLastError());
       residual(m, 0, outer_dtype, f, u, r64, false, s);
     }
-    if (outer > p.max_outer) outer = p.max_outer;
+    if (outer > p.max_outer) {
+      // the refinement steps ran out: report the residual of the last correction
+      outer = p.max_outer;
+      dot(m, 0, HHG_F64, r64, r64, 7, RED_STORE, false, s);
+      rel = std::sqrt(read_scalar(m, 7, s)) / nf;
+    }
     if (rel > p.tol) status = HHG_ERR_NOT_CONVERGED;
   }
   HHG_CUDA(cudaStreamSynchronize(s));

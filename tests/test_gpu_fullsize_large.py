@@ -165,5 +165,8 @@ def test_large_bf16k_mixed_solve_residual(big):
     r = torch.empty_like(x)
     H.hhg_residual(m.h, 0, f, x, r, H.HHG_F64)
     r_lib = r[torch.as_tensor(sample, device="cuda")].cpu().numpy()
-    fmax = float(torch.max(torch.abs(f)))
-    assert np.max(np.abs(r_lib - r_or)) <= 1e-12 * fmax, np.max(np.abs(r_lib - r_or))
+    # both are FP64 sums of a row's terms, whose size is bounded by
+    # 2 kmax sum_d |c_d| max|x| (the volume stencil; f itself is far smaller)
+    c = np.abs(m.stencils(0, 0)[0]).sum()
+    scale = 2 * 1.5 * c * float(torch.max(torch.abs(x)))
+    assert np.max(np.abs(r_lib - r_or)) <= 1e-13 * scale, (np.max(np.abs(r_lib - r_or)), scale)
