@@ -78,8 +78,11 @@ typedef enum {
 typedef enum {
     HHG_SOLVE_FP64 = 0,        /* plain FP64 GMG-preconditioned CG */
     HHG_SOLVE_MIXED = 1,       /* FP64 iterative refinement around FP32 GMG-CG */
-    HHG_SOLVE_MIXED_KBF16 = 2, /* as MIXED, bfloat16 k in the FP32 inner solve */
-    HHG_SOLVE_MG = 3           /* FP64 multigrid as the solver: u <- V(nu1,nu2)(f, u) (Sec. 7.2) */
+    HHG_SOLVE_MIXED_KBF16 = 2, /* as MIXED with k rounded to bfloat16 everywhere: the FP32 inner solve and
+                                  the FP64 outer residual, so u is the discrete solution of the rounded k */
+    HHG_SOLVE_MG = 3,          /* FP64 multigrid as the solver: u <- V(nu1,nu2)(f, u) (Sec. 7.2) */
+    HHG_SOLVE_MIXED_KBF16_INNER = 4 /* bfloat16 k in the FP32 inner solve only, the FP64 k in the outer
+                                  residual: u is the discrete solution of the FP64 k */
 } hhg_solve_mode;
 
 typedef enum {
@@ -361,6 +364,18 @@ int hhg_get_option(hhg_mesh mesh, const char* key, double* value);
  * groups), so none sets it and the call returns HHG_OK; it is kept for kernels
  * with bounded waits.  Synchronous; clears the word. */
 int hhg_device_status(hhg_mesh mesh);
+
+/* Arithmetic peak probe (a measurement aid, not part of the method): one
+ * launch of `blocks` blocks of 256 threads on `stream`, every thread running
+ * 8 independent multiply-add chains for `iters` steps.  kind 0: FP64 fma,
+ * 1: FP32 fma, 2: packed FP32x2 fma (two per instruction).  out_dev: device
+ * array of at least blocks * 256 doubles (each thread's chain sum, written
+ * so nothing is folded away).  *flops receives the floating-point operations
+ * the launch performs (2 per multiply-add); divide by the launch's
+ * CUDA-event time for the rate.  Asynchronous.  HHG_ERR_ARG for an unknown
+ * kind, non-positive sizes or NULL pointers; HHG_ERR_CUDA if the launch
+ * fails. */
+int hhg_alu_probe(int kind, int blocks, int iters, void* out_dev, double* flops, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hhg_last_error(void);

@@ -261,7 +261,7 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
   if (p.max_outer <= 0) p.max_outer = 20;
   if (p.maxit <= 0) p.maxit = 200;
   HHG_REQUIRE(p.tol > 0, "tol must be positive");
-  HHG_REQUIRE(p.mode >= 0 && p.mode <= 3, "unknown solve mode");
+  HHG_REQUIRE(p.mode >= 0 && p.mode <= 4, "unknown solve mode");
   HHG_REQUIRE(p.op >= 0 && p.op <= 3, "unknown operator");
   HHG_REQUIRE(p.op != 3 || m.tensor_set, "hhg_set_tensor_coefficient must be called first");
   HHG_REQUIRE(p.op == 0 || p.mode == HHG_SOLVE_MG, "the Vol+Face, nodal and tensor operators are solved with HHG_SOLVE_MG");
@@ -276,7 +276,7 @@ int solve(Mesh& m, const hhg_solve_params& p_in, const double* f, double* u, hhg
   const int outer_dtype = p.mode == HHG_SOLVE_MIXED_KBF16 ? kF64KBF16 : HHG_F64;
   int inner_dtype = HHG_F64;
   if (p.mode == HHG_SOLVE_MIXED) inner_dtype = HHG_F32;
-  if (p.mode == HHG_SOLVE_MIXED_KBF16) inner_dtype = HHG_F32_KBF16;
+  if (p.mode == HHG_SOLVE_MIXED_KBF16 || p.mode == HHG_SOLVE_MIXED_KBF16_INNER) inner_dtype = HHG_F32_KBF16;
   prepare(m, inner_dtype, p.smoother, s);
   if (inner_dtype != HHG_F64) prepare(m, HHG_F64, HHG_SMOOTH_JACOBI, s);
   // ||f||

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhhg.so")
 
 HHG_F64, HHG_F32, HHG_F32_KBF16 = 0, 1, 2
 HHG_SMOOTH_JACOBI, HHG_SMOOTH_CHEBYSHEV, HHG_SMOOTH_LEARNED = 0, 1, 2
-HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16, HHG_SOLVE_MG = 0, 1, 2, 3
+HHG_SOLVE_FP64, HHG_SOLVE_MIXED, HHG_SOLVE_MIXED_KBF16, HHG_SOLVE_MG, HHG_SOLVE_MIXED_KBF16_INNER = 0, 1, 2, 3, 4
 HHG_OP_SCALED, HHG_OP_VOLFACE, HHG_OP_NODAL, HHG_OP_TENSOR = 0, 1, 2, 3
 STATUS = {0: "HHG_OK", -1: "HHG_ERR_ARG", -2: "HHG_ERR_CUDA", -3: "HHG_ERR_NOMEM",
           -4: "HHG_ERR_NOT_CONVERGED", -5: "HHG_ERR_TIMEOUT", -6: "HHG_ERR_STATE"}
@@ -95,6 +95,7 @@ def _load():
         "hhg_learned_get_weights": [P, P],
         "hhg_learned_forward": [P, I, P, P, P],
         "hhg_learned_loss_grad": [P, I, P, P, C.POINTER(D), P, P],
+        "hhg_alu_probe": [I, I, I, P, C.POINTER(D), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -305,6 +306,13 @@ def hhg_learned_loss_grad(mesh, depth, r, e, stream=None):
     g = np.zeros(N_LEARNED_WEIGHTS, dtype=np.float64)
     _check(_lib.hhg_learned_loss_grad(mesh, depth, _ptr(r), _ptr(e), C.byref(loss), g.ctypes.data, _stream(stream)))
     return loss.value, g
+
+
+def hhg_alu_probe(kind, blocks, iters, out, stream=None):
+    """Launch the multiply-add peak probe; returns the launch's flop count."""
+    flops = C.c_double()
+    _check(_lib.hhg_alu_probe(kind, blocks, iters, _ptr(out), C.byref(flops), _stream(stream)))
+    return flops.value
 
 
 def hhg_device_status(mesh):

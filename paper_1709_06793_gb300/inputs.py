@@ -264,9 +264,22 @@ def f_sine_tensor(x):
 
 
 def k_large(x):
-    """1 + 0.5 sin(4 pi x) cos(4 pi y) sin(4 pi z)."""
+    """1 + 0.5 sin(4 pi x) cos(4 pi y) sin(4 pi z).  x: (n, 3) float64, a numpy
+    array or a torch tensor (then evaluated on the tensor's device)."""
+    if hasattr(x, "sin"):  # torch tensor
+        a = 4 * np.pi * x
+        return 1.0 + 0.5 * a[:, 0].sin() * a[:, 1].cos() * a[:, 2].sin()
     x = np.asarray(x, dtype=np.float64)
     return 1.0 + 0.5 * np.sin(4 * np.pi * x[:, 0]) * np.cos(4 * np.pi * x[:, 1]) * np.sin(4 * np.pi * x[:, 2])
+
+
+def u_wave(x):
+    """sin(9 x) cos(7 y): a smooth non-polynomial operand for apply timings
+    (numpy array or torch tensor, as k_large)."""
+    if hasattr(x, "sin"):
+        return (9 * x[:, 0]).sin() * (7 * x[:, 1]).cos()
+    x = np.asarray(x, dtype=np.float64)
+    return np.sin(9 * x[:, 0]) * np.cos(7 * x[:, 1])
 
 
 def fourier_field(seed, n_modes=8):

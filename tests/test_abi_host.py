@@ -128,6 +128,10 @@ def test_bad_arguments_are_reported(H):
     with pytest.raises(H.HHGError, match="host-only"):
         H.hhg_apply_scaled(m.h, 0, 1, 2, H.HHG_F32)
     m.close()
+    # the peak probe checks its arguments before it launches anything
+    for kind, blocks, iters, out in ((3, 1, 1, 16), (0, 0, 1, 16), (1, 1, 0, 16), (2, 1, 1, None)):
+        with pytest.raises(H.HHGError, match="hhg_alu_probe"):
+            H.hhg_alu_probe(kind, blocks, iters, out)
 
 
 def test_size_limits_and_empty_meshes_are_reported(H):

@@ -15,3 +15,37 @@ def test_code_only_sees_code_changes():
     b = "int f(int x) {\n  return x + 2;\n}\n"
     assert bench._code_only(a) != bench._code_only(b)
 
+
+def test_unknown_count_matches_the_oracle_meshes():
+    """unique unknowns = nodes off the boundary: the 6-tet cube at level 8 has
+    255^3; the 24- and 12-tet cubes agree with the oracle's level meshes."""
+    from oracle import hhg_oracle as O
+    from paper_1709_06793_gb300 import inputs as I
+    _, T = I.kuhn_cube()
+    assert bench.unknowns_of(T, 8) == 255 ** 3
+    for mesh, levels in ((I.cube24, (1, 2, 3, 4)), (I.cube12, (1, 2, 3)), (I.unit_tet, (2, 3))):
+        V, T = mesh()
+        for level in levels:
+            lm = O.LevelMesh(O.MacroMesh(V, T), level)
+            assert bench.unknowns_of(T, level) == len(lm.unknowns), (mesh.__name__, level)
+
+
+def test_reference_arm_line_states_the_sample_it_timed(monkeypatch, capsys):
+    """The reference arm times the oracle at its sample level on every host
+    core and says so in its line (level, processes, cores)."""
+    import json
+
+    monkeypatch.setattr(bench, "CPU_LEVEL", 2)
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+
+    class Args:
+        gpus, steps, warmup = 1, 2, 1
+
+    out = bench.run_reference(Args())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line == json.loads(json.dumps(out))
+    assert line["impl"] == "reference" and line["config"]["level"] == 2
+    assert line["config"]["processes"] == line["cpu_baseline"]["cores"] == bench.host_info()["nproc"]
+    assert "level 2" in line["config"]["workload"] and "level 9" not in line["config"]["workload"]
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]

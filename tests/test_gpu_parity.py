@@ -313,8 +313,11 @@ def test_lambda_max_parity(H):
         assert abs(lam - Hh.lam[4 - depth]) <= 1e-10 * Hh.lam[4 - depth]
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 4])
 def test_solve_matches_oracle_discrete_solution(H, mode):
+    """Modes 0, 1 and 4 (BF16 k in the inner solve only) reach the discrete
+    solution of the FP64 k; mode 2 (BF16 k throughout) that of k rounded to
+    bfloat16."""
     V, T = I.kuhn_cube()
     level = 5
     c = Case(H, V, T, level, 2, I.k_cube)
