@@ -78,7 +78,7 @@ def _kernel_sha():
     """Hash of the scaled apply's sources (kernels and shared constants),
     code only."""
     h = hashlib.sha256()
-    for f in ("apply.cu", "hhg_internal.h"):
+    for f in ("apply.cu", "march.cu", "hhg_internal.h"):
         h.update(_code_only(open(os.path.join(ROOT, "paper_1709_06793_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
@@ -896,7 +896,7 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
             "peak_source": f"{src} hbm_gbs (burst)",
-            "kernel": "scaled_op_kernel<float,__nv_bfloat16,APPLY> (volume rows) + boundary_only_kernel (interface "
+            "kernel": "march_kernel<float,__nv_bfloat16,2,APPLY> (volume rows) + boundary_only_kernel (interface "
                       "rows, concurrent on a forked stream); achieved = algorithmic bytes / CUDA-event time of the "
                       "pair on the caller's stream",
             "algorithmic_bytes_per_launch": algo_bytes, "algorithmic_bytes_per_unknown": 10,

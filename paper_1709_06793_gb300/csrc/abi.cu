@@ -406,6 +406,9 @@ int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
       set_kseg(m, (int)value, m.korder);
     } else if (k == "korder") {
       set_kseg(m, m.kseg, (int)value);
+    } else if (k == "vkernel") {
+      if (value != 0 && value != 1 && value != 2) throw Error{HHG_ERR_ARG, "vkernel must be 0, 1 or 2"};
+      m.vkernel = (int)value;
     } else if (k == "cheb_degree") {
       if (value < 1 || value > 16) throw Error{HHG_ERR_ARG, "cheb_degree must be in [1, 16]"};
       m.cheb_degree = (int)value;
@@ -433,6 +436,7 @@ int hhg_get_option(hhg_mesh mesh, const char* key, double* value) {
     const std::string k(key);
     if (k == "kseg") *value = m.kseg;
     else if (k == "korder") *value = m.korder;
+    else if (k == "vkernel") *value = m.vkernel;
     else if (k == "cheb_degree") *value = m.cheb_degree;
     else if (k == "cheb_lo") *value = m.cheb_lo;
     else if (k == "cheb_hi") *value = m.cheb_hi;

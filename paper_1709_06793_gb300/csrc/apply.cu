@@ -702,6 +702,7 @@ static void init_typed() {
 
 // Launch configurations are computed once, outside any stream capture.
 void init_launch_configs(int dtype) {
+  init_march_configs(dtype);
   if (dtype == HHG_F64 || dtype == kF64KBF16)
     init_typed<double, double>();
   else if (dtype == HHG_F32)
@@ -711,7 +712,7 @@ void init_launch_configs(int dtype) {
 }
 
 template <class T, class KT, int MODE>
-static void launch_typed(const Mesh& m, int depth, const OpArgs& a, const void* kptr, cudaStream_t s) {
+static void launch_typed(const Mesh& m, int depth, int dtype, const OpArgs& a, const void* kptr, cudaStream_t s) {
   const Depth& Dh = m.depth[depth];
   const DepthDev& D = Dh.dev;
   const int n_items = a.nc_only ? D.n_items_nc : D.n_items;
@@ -728,10 +729,22 @@ static void launch_typed(const Mesh& m, int depth, const OpArgs& a, const void* 
     boundary_only_kernel<T, KT, MODE><<<(n_b + 127) / 128, 128, 0, m.side>>>(D, p, n_b);
     HHG_CUDA(cudaGetLastError());
     HHG_CUDA(cudaEventRecord(m.side_join, m.side));
-    const int blocks = std::min((n_items + 3) / 4, m.num_sms * occ);
-    scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, 0, m.d_error);
-    HHG_CUDA(cudaGetLastError());
+    if (m.vkernel >= 1) {
+      launch_march(m, depth, dtype, (OpMode)MODE, a, s);
+    } else {
+      const int blocks = std::min((n_items + 3) / 4, m.num_sms * occ);
+      scaled_op_kernel<T, KT, MODE><<<blocks, 128, ring_bytes<T, KT>(), s>>>(D, p, n_items, 0, m.d_error);
+      HHG_CUDA(cudaGetLastError());
+    }
     HHG_CUDA(cudaStreamWaitEvent(s, m.side_join, 0));
+    return;
+  }
+  if (m.vkernel >= 1 && n_items > 0) {
+    launch_march(m, depth, dtype, (OpMode)MODE, a, s);
+    if (n_b > 0) {
+      boundary_only_kernel<T, KT, MODE><<<(n_b + 127) / 128, 128, 0, s>>>(D, p, n_b);
+      HHG_CUDA(cudaGetLastError());
+    }
     return;
   }
   const int blocks = std::min((work + 3) / 4, m.num_sms * occ);
@@ -743,13 +756,13 @@ template <int MODE>
 static void launch_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, cudaStream_t s) {
   const Depth& Dh = m.depth[depth];
   if (dtype == HHG_F64)
-    launch_typed<double, double, MODE>(m, depth, a, Dh.k64, s);
+    launch_typed<double, double, MODE>(m, depth, dtype, a, Dh.k64, s);
   else if (dtype == kF64KBF16)
-    launch_typed<double, double, MODE>(m, depth, a, Dh.k16d, s);
+    launch_typed<double, double, MODE>(m, depth, dtype, a, Dh.k16d, s);
   else if (dtype == HHG_F32)
-    launch_typed<float, float, MODE>(m, depth, a, Dh.k32, s);
+    launch_typed<float, float, MODE>(m, depth, dtype, a, Dh.k32, s);
   else
-    launch_typed<float, __nv_bfloat16, MODE>(m, depth, a, Dh.k16, s);
+    launch_typed<float, __nv_bfloat16, MODE>(m, depth, dtype, a, Dh.k16, s);
 }
 
 void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {

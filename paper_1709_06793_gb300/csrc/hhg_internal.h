@@ -74,6 +74,13 @@ struct DepthDev {
   const int4* items;     // volume work: (tile = slot<<20 | j0<<10 | i0, k0, k1, -) per warp item
   int n_items;           // items of all active tets
   int n_items_nc;        // items of tets above the coarsest level (prefix)
+  const int4* mitems;    // column-march work: (pair, i0 | j0<<16, k0, k1) per warp item
+  const int2* pairs;     // (slot a, slot b or -1): pairs of same-level tets, then every slot alone
+  int n_mitems;          // items over the pairs (packed FP32x2 kernels)
+  int n_mitems_nc;       // of those, items of tets above the coarsest level (prefix)
+  const int4* sitems;    // the same over single tets (FP64 kernels)
+  int n_sitems;
+  int n_sitems_nc;
   const int* bstart;     // boundary unique nodes: copies bstart[b]..bstart[b+1]
   const BCopy* bcopies;
   const unsigned char* bdir;  // 1 = Dirichlet
@@ -108,6 +115,9 @@ struct Depth {
   std::vector<double> h_mass;         // [slot][16][15]
   std::vector<int4> h_items;
   int n_items = 0, n_items_nc = 0;
+  std::vector<int4> h_mitems, h_sitems;
+  std::vector<int2> h_pairs;
+  int n_mitems = 0, n_mitems_nc = 0, n_sitems = 0, n_sitems_nc = 0;
   std::vector<int> h_bstart;
   std::vector<BCopy> h_bcopies;
   std::vector<unsigned char> h_bdir;
@@ -205,6 +215,8 @@ struct Mesh {
   double cheb_lo = 0.3, cheb_hi = 1.1;
   int power_its = 15;
   int kseg = 32;                  // planes per volume work item (k-march segment)
+  int vkernel = 2;                // volume kernel: 0 tile march (apply.cu); column march (march.cu): 1 with
+                                  // two same-level tets per packed FP32x2 register pair, 2 one tet per warp
   int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)
   void* learned = nullptr;
@@ -252,6 +264,7 @@ void stencils_for(const Mesh& m, int tet, int level, double* out16x14);
 void elements_for(const Mesh& m, int tet, int level, double* out6x16);
 void* dalloc(Depth& d, size_t bytes);
 void build_items(const Mesh& m, Depth& D);
+void build_march_items(const Mesh& m, Depth& D);
 void set_kseg(Mesh& m, int kseg, int korder);
 
 // ---- kernels (apply.cu / mg.cu) ----------------------------------------------
@@ -271,6 +284,12 @@ struct OpArgs {
 };
 
 void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
+// volume rows of the scaled operator by the column march (march.cu)
+void launch_march(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
+void init_march_configs(int dtype);
+// bytes past the end of every coefficient array (bulk copies of whole 16-byte
+// chunks may reach into it)
+constexpr int kCoefPad = 64;
 void launch_nodal_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
 // scaled launch followed by the nodal-integration rows of macro vertices and edges (eq. "modst")
 void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);

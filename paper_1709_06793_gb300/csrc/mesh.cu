@@ -404,6 +404,7 @@ void build_items(const Mesh& m, Depth& D) {
   D.n_items_nc = (int)D.h_items.size();
   D.h_items.insert(D.h_items.end(), by_class[1].begin(), by_class[1].end());
   D.n_items = (int)D.h_items.size();
+  build_march_items(m, D);
 }
 
 static void build_depth(Mesh& m, int d) {
@@ -582,6 +583,13 @@ void set_kseg(Mesh& m, int kseg, int korder) {
       D.dev.items = reupload(D, const_cast<int4*>(D.dev.items), D.h_items);
       D.dev.n_items = D.n_items;
       D.dev.n_items_nc = D.n_items_nc;
+      D.dev.mitems = reupload(D, const_cast<int4*>(D.dev.mitems), D.h_mitems);
+      D.dev.sitems = reupload(D, const_cast<int4*>(D.dev.sitems), D.h_sitems);
+      D.dev.pairs = reupload(D, const_cast<int2*>(D.dev.pairs), D.h_pairs);
+      D.dev.n_mitems = D.n_mitems;
+      D.dev.n_mitems_nc = D.n_mitems_nc;
+      D.dev.n_sitems = D.n_sitems;
+      D.dev.n_sitems_nc = D.n_sitems_nc;
     }
   }
 }
@@ -600,6 +608,13 @@ static void upload_depth(Depth& D) {
   D.dev.items = upload(D, D.h_items);
   D.dev.n_items = D.n_items;
   D.dev.n_items_nc = D.n_items_nc;
+  D.dev.mitems = upload(D, D.h_mitems);
+  D.dev.sitems = upload(D, D.h_sitems);
+  D.dev.pairs = upload(D, D.h_pairs);
+  D.dev.n_mitems = D.n_mitems;
+  D.dev.n_mitems_nc = D.n_mitems_nc;
+  D.dev.n_sitems = D.n_sitems;
+  D.dev.n_sitems_nc = D.n_sitems_nc;
   D.dev.bstart = upload(D, D.h_bstart);
   D.dev.bcopies = upload(D, D.h_bcopies);
   D.dev.bdir = upload(D, D.h_bdir);

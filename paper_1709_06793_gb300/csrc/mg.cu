@@ -150,10 +150,16 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
     Depth& D = m.depth[d];
     const size_t n = std::max<long long>(D.n_stored, 1);
     if (!D.k64) {
-      D.k64 = static_cast<double*>(dalloc(D, n * 8));
-      D.k16d = static_cast<double*>(dalloc(D, n * 8));
-      D.k32 = static_cast<float*>(dalloc(D, n * 4));
-      D.k16 = static_cast<__nv_bfloat16*>(dalloc(D, n * 2 + 16));  // +16: staged as 4-byte words
+      // kCoefPad zero bytes past the end: the volume kernel's bulk copies
+      // move whole 16-byte chunks and may reach past the last node
+      D.k64 = static_cast<double*>(dalloc(D, n * 8 + kCoefPad));
+      D.k16d = static_cast<double*>(dalloc(D, n * 8 + kCoefPad));
+      D.k32 = static_cast<float*>(dalloc(D, n * 4 + kCoefPad));
+      D.k16 = static_cast<__nv_bfloat16*>(dalloc(D, n * 2 + kCoefPad));
+      HHG_CUDA(cudaMemsetAsync(D.k64, 0, n * 8 + kCoefPad, s));
+      HHG_CUDA(cudaMemsetAsync(D.k16d, 0, n * 8 + kCoefPad, s));
+      HHG_CUDA(cudaMemsetAsync(D.k32, 0, n * 4 + kCoefPad, s));
+      HHG_CUDA(cudaMemsetAsync(D.k16, 0, n * 2 + kCoefPad, s));
     }
   }
   Depth& D0 = m.depth[0];
