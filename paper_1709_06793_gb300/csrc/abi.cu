@@ -407,7 +407,7 @@ int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
     } else if (k == "korder") {
       set_kseg(m, m.kseg, (int)value);
     } else if (k == "vkernel") {
-      if (value != 0 && value != 1 && value != 2) throw Error{HHG_ERR_ARG, "vkernel must be 0, 1 or 2"};
+      if (value != 0 && value != 1) throw Error{HHG_ERR_ARG, "vkernel must be 0 or 1"};
       m.vkernel = (int)value;
     } else if (k == "cheb_degree") {
       if (value < 1 || value > 16) throw Error{HHG_ERR_ARG, "cheb_degree must be in [1, 16]"};

@@ -215,8 +215,7 @@ struct Mesh {
   double cheb_lo = 0.3, cheb_hi = 1.1;
   int power_its = 15;
   int kseg = 32;                  // planes per volume work item (k-march segment)
-  int vkernel = 2;                // volume kernel: 0 tile march (apply.cu); column march (march.cu): 1 with
-                                  // two same-level tets per packed FP32x2 register pair, 2 one tet per warp
+  int vkernel = 1;                // volume kernel: 1 column march (march.cu), 0 tile march (apply.cu)
   int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)
   void* learned = nullptr;
