@@ -349,12 +349,20 @@ int hhg_dot(hhg_mesh mesh, int depth, const void* x_dev, const void* y_dev, int 
 int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, double* u_dev,
               hhg_solve_stats* stats, void* stream);
 
-/* Tuning options of a mesh (not part of the method): "kseg" planes per
- * volume work item of the k-march and "korder" (0: longest item first, 1:
- * items ordered by plane window) -- both rebuild the work lists and
- * synchronise the device --, "cheb_degree", "cheb_lo", "cheb_hi" (Chebyshev interval as
- * fractions of lambda_max) and "power_its" (lambda_max estimate).  Unknown
- * keys or out-of-range values: HHG_ERR_ARG. */
+/* Options of a mesh.  The method: "kappa" (0 or 1): 1 scales every
+ * direction of gray type (a positive entry of the macro tetrahedron's
+ * reference volume stencil, Sec. 4.2) with (k_min(x) + k_min(y))/2 instead
+ * of (k_x + k_y)/2, k_min(x) the minimum of k over x and its edge neighbours
+ * inside that macro tetrahedron (Sec. 4, eq. "defKmin": the pre-asymptotic
+ * modification that keeps the form coercive); all modes of the scaled
+ * operator and the solvers use it; synchronises the device.  Tuning (not
+ * part of the method): "kseg" planes per volume work item of the k-march and
+ * "korder" (0: longest item first, 1: items ordered by plane window) -- both
+ * rebuild the work lists and synchronise the device --, "vkernel" (1: the
+ * column-march volume kernel, 0: the tile-march one), "cheb_degree",
+ * "cheb_lo", "cheb_hi" (Chebyshev interval as fractions of lambda_max) and
+ * "power_its" (lambda_max estimate).  Unknown keys or out-of-range values:
+ * HHG_ERR_ARG. */
 int hhg_set_option(hhg_mesh mesh, const char* key, double value);
 int hhg_get_option(hhg_mesh mesh, const char* key, double* value);
 

@@ -17,6 +17,10 @@ It computes, from the paper's definitions and nothing else,
 * the nodal-integration operator of eq. "standardfe": mean vertex k times A_t;
 * the "scale Vol+Face" operator of eq. "modst" (nodal rows on macro vertices
   and edges, scaled rows elsewhere);
+* the pre-asymptotic modification of Sec. 4 (eq. "defKmin"): on the edges of
+  "gray type" (positive reference stencil entry) of a macro tetrahedron the
+  scaling (k_i+k_j)/2 becomes (k_min(x_i)+k_min(x_j))/2, k_min the minimum
+  of k over a node and its edge neighbours inside that macro tetrahedron;
 * the consistent P1 mass matrix (right-hand side f_h = M I_h f, Sec. 7.2);
 * global assembly over unique nodes (nodes on macro faces/edges/vertices are
   shared by all macro tetrahedra that contain them, Sec. 2.1), homogeneous
@@ -188,6 +192,59 @@ def element_matrices(X, kv, kind):
 
 
 # ----------------------------------------------------------------------------
+# Pre-asymptotic modification (Sec. 4, eq. "defKmin")
+# ----------------------------------------------------------------------------
+
+# the 14 stencil directions (di, dj, dk): e1, e2, e3, e1-e2, e1-e3, e2-e3,
+# e1-e2+e3 and their negatives (the edge directions of the refined mesh)
+STENCIL_DIRS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, -1, 0), (1, 0, -1), (0, 1, -1), (1, -1, 1)]
+STENCIL_DIRS = STENCIL_DIRS + [(-a, -b, -c) for (a, b, c) in STENCIL_DIRS]
+
+
+def reference_volume_stencil(V, tet):
+    """Laplacian stencil (14 off-centre entries, STENCIL_DIRS order) of a node
+    inside the macro tetrahedron with vertices V[tet] in refinement order:
+    the row of node (1,1,1) of the level-2 refinement of that tetrahedron
+    alone (the volume stencil does not depend on the level or the node)."""
+    lm = LevelMesh(MacroMesh(np.asarray(V, dtype=np.float64)[list(tet)], np.array([[0, 1, 2, 3]])), 2)
+    A = lm.assemble(None, "laplace").tocsr()
+    x = lm.local[0][1, 1, 1]
+    return np.array([A[x, lm.local[0][1 + a, 1 + b, 1 + c]] for (a, b, c) in STENCIL_DIRS])
+
+
+def gray_directions(V, tet, tol=1e-14):
+    """Directions of gray type (Sec. 4.2: edges with a positive reference
+    stencil entry), as a boolean mask over STENCIL_DIRS."""
+    return reference_volume_stencil(V, tet) > tol
+
+
+def tet_kmin(lm, k, t):
+    """k_min(x) of eq. "defKmin" for the nodes of macro tetrahedron t: the
+    minimum of k over x and every node joined to x by an edge that belongs to
+    the macro tetrahedron (the edges of its micro tetrahedra).  Full-size
+    array; entries of nodes outside t are k itself."""
+    k = np.asarray(k, dtype=np.float64)
+    km = k.copy()
+    ids = lm.micro[t]
+    np.minimum.at(km, ids.reshape(-1), np.repeat(k[ids].min(axis=1), 4))
+    return km
+
+
+def kmin_element(A, kv, kmv, gray_pair):
+    """Scaled element matrix with the modification: entry (a, b) scaled by
+    (k_a + k_b)/2, or by (kmin_a + kmin_b)/2 where gray_pair[:, a, b]; the
+    diagonal by the zero row sum."""
+    A = np.asarray(A, dtype=np.float64)
+    K = 0.5 * (kv[:, :, None] + kv[:, None, :])
+    Km = 0.5 * (kmv[:, :, None] + kmv[:, None, :])
+    M = np.where(gray_pair, Km, K) * A
+    idx = np.arange(4)
+    M[:, idx, idx] = 0.0
+    M[:, idx, idx] = -M.sum(axis=2)
+    return M
+
+
+# ----------------------------------------------------------------------------
 # Macro mesh topology
 # ----------------------------------------------------------------------------
 
@@ -306,7 +363,23 @@ class LevelMesh:
         ids = self.micro[t]
         X = self.coords[ids]
         kv = None if k is None else np.asarray(k, dtype=np.float64)[ids]
+        if kind == "kmin":
+            return ids, kmin_element(p1_stiffness(X), kv, tet_kmin(self, k, t)[ids], self._gray_pairs(t))
         return ids, element_matrices(X, kv, kind)
+
+    def _gray_pairs(self, t):
+        """(ne, 4, 4) mask: the micro edge (a, b) of each micro tetrahedron of
+        macro tetrahedron t runs along a gray direction of t."""
+        gray = gray_directions(self.macro.V, self.macro.T[t])
+        mt = self.micro_index  # (ne, 4, 3) index coordinates of the vertices
+        out = np.zeros((len(mt), 4, 4), dtype=bool)
+        lut = {d: g for d, g in zip(STENCIL_DIRS, gray)}
+        for a in range(4):
+            for b in range(4):
+                if a != b:
+                    dv = mt[:, b, :] - mt[:, a, :]
+                    out[:, a, b] = [lut[tuple(v)] for v in dv]
+        return out
 
     def assemble(self, k, kind="scaled"):
         """Full n x n matrix (Dirichlet rows and columns kept)."""

@@ -406,6 +406,17 @@ int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
       set_kseg(m, (int)value, m.korder);
     } else if (k == "korder") {
       set_kseg(m, m.kseg, (int)value);
+    } else if (k == "kappa") {
+      if (value != 0 && value != 1) throw Error{HHG_ERR_ARG, "kappa must be 0 or 1"};
+      m.kappa = value != 0;
+      if (m.kappa && m.coef_set && m.device) {
+        compute_kmin(m, nullptr);
+        HHG_CUDA(cudaDeviceSynchronize());
+      }
+      // the operator changed: coarse inverses and eigenvalue estimates are stale
+      for (int o = 0; o < 4; ++o)
+        for (int t = 0; t < 4; ++t) m.cinv_ready[o][t] = false;
+      for (Depth& D : m.depth) D.lam = 0.0;
     } else if (k == "vkernel") {
       if (value != 0 && value != 1) throw Error{HHG_ERR_ARG, "vkernel must be 0 or 1"};
       m.vkernel = (int)value;
@@ -437,6 +448,7 @@ int hhg_get_option(hhg_mesh mesh, const char* key, double* value) {
     if (k == "kseg") *value = m.kseg;
     else if (k == "korder") *value = m.korder;
     else if (k == "vkernel") *value = m.vkernel;
+    else if (k == "kappa") *value = m.kappa ? 1 : 0;
     else if (k == "cheb_degree") *value = m.cheb_degree;
     else if (k == "cheb_lo") *value = m.cheb_lo;
     else if (k == "cheb_hi") *value = m.cheb_hi;

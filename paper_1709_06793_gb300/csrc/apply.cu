@@ -766,6 +766,10 @@ static void launch_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, cu
 }
 
 void launch_scaled_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
+  if (m.kappa) {  // the pre-asymptotic modification of Sec. 4 (kappa.cu)
+    launch_kappa_op(m, depth, dtype, mode, a, s);
+    return;
+  }
   switch (mode) {
     case OP_APPLY: launch_mode<OP_APPLY>(m, depth, dtype, a, s); break;
     case OP_RESID: launch_mode<OP_RESID>(m, depth, dtype, a, s); break;

@@ -97,6 +97,7 @@ struct DepthDev {
   const int* vf;               // interface nodes on macro vertices/edges (not Dirichlet): indices into bstart
   int n_vf;
   int n_vf_nc;
+  const unsigned* gray;         // [slot] bit d set: direction d of the volume stencil is of gray type (> 0)
   const int* fslot;            // slot of the same tet at depth-1 (-1 at depth 0)
   const unsigned char* mult;   // [slot][16] copies of a node of that face mask
 };
@@ -149,6 +150,14 @@ struct Depth {
   double* k64 = nullptr;
   float* k32 = nullptr;
   __nv_bfloat16* k16 = nullptr;
+  // k_min of eq. "defKmin" per stored copy (the minimum over the copy's
+  // neighbourhood inside its own tet), per precision; set while the mesh's
+  // kappa option is on
+  double* kmin64 = nullptr;
+  double* kmin16d = nullptr;
+  float* kmin32 = nullptr;
+  __nv_bfloat16* kmin16 = nullptr;
+  std::vector<unsigned> h_gray;
   // multigrid workspace per precision (allocated lazily): 0 = f64, 1 = f32
   // slots: 0 F (depth>0) / CG r (depth 0), 1 U / CG z, 2 V-cycle residual,
   // 3 CG p, 4 smoother ping-pong, 5-6 Chebyshev updates, 7 CG q, 8 inner solution
@@ -216,6 +225,7 @@ struct Mesh {
   int power_its = 15;
   int kseg = 32;                  // planes per volume work item (k-march segment)
   int vkernel = 1;                // volume kernel: 1 column march (march.cu), 0 tile march (apply.cu)
+  bool kappa = false;             // scaled operator with k_min on gray directions (eq. "defKmin", kappa.cu)
   int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)
   void* learned = nullptr;
@@ -302,5 +312,8 @@ void ensure_tensor_stencils(Mesh& m);
 void launch_nodal_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, const void* dinv, void* tmp,
                      cudaStream_t s);
 void launch_mass_apply(const Mesh& m, int depth, int dtype, const void* u, void* y, cudaStream_t s);
+// scaled operator with the pre-asymptotic modification (kappa.cu)
+void compute_kmin(Mesh& m, cudaStream_t s);
+void launch_kappa_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s);
 
 }  // namespace hhg

@@ -596,6 +596,17 @@ void set_kseg(Mesh& m, int kseg, int korder) {
 
 static void upload_depth(Depth& D) {
   D.dev.tets = upload(D, D.h_tets);
+  // gray directions of each slot's volume stencil (positive off-centre
+  // entries, Sec. 4.2), relative to the stencil's largest entry
+  D.h_gray.assign(D.h_tets.size(), 0u);
+  for (size_t sl = 0; sl < D.h_tets.size(); ++sl) {
+    const double* st = &D.h_sten[sl * 16 * kNDir];  // mask 0: the volume row
+    double mx = 0;
+    for (int d = 0; d < kNDir; ++d) mx = std::max(mx, std::abs(st[d]));
+    for (int d = 0; d < kNDir; ++d)
+      if (st[d] > 1e-12 * mx) D.h_gray[sl] |= 1u << d;
+  }
+  D.dev.gray = upload(D, D.h_gray);
   D.dev.sten64 = upload(D, D.h_sten);
   std::vector<float> s32(D.h_sten.begin(), D.h_sten.end());
   D.dev.sten32 = upload(D, s32);

@@ -177,6 +177,7 @@ void set_coefficient(Mesh& m, const double* k, cudaStream_t s) {
     HHG_CUDA(cudaGetLastError());
   }
   m.coef_set = true;
+  if (m.kappa) compute_kmin(m, s);
   for (int o = 0; o < 4; ++o)
     for (int t = 0; t < 4; ++t) m.cinv_ready[o][t] = false;
   for (Depth& D : m.depth)
