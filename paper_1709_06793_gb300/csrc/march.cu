@@ -256,6 +256,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
     };
 
     int st_c = st_i;  // stage of the next plane to read (plane q_first)
+    // every warp is done with the previous item's stages (the last one read
+    // is the first one this item fills)
+    __syncthreads();
 #pragma unroll
     for (int t = 0; t < S - 1; ++t) issue();
 

@@ -197,3 +197,34 @@ def test_learned_level7_grf_properties(H):
             assert s_["smoother_used"] == H.HHG_SMOOTH_LEARNED
     assert its["learned"] < its["plain"], its
     m.close()
+
+
+@pytest.mark.parametrize("kseg", [4, 16, 32])
+def test_residual_is_f_minus_the_apply_at_full_size(H, kseg):
+    """Residual mode r = f - A u and the apply y = A u come from the same row
+    arithmetic, so r == f - y bitwise on every stored node, at the level-8
+    cube in every precision and work-list segmentation (the work items'
+    shared staging must not let one item overwrite rows another still reads)."""
+    V, T = I.kuhn_cube()
+    m = H.Mesh(V, T, 8, 2)
+    off, lev, n = m.layout(0)
+    X = torch.from_numpy(m.coords(0)).cuda()
+    H.hhg_set_coefficient(m.h, I.k_large(X))
+    H.hhg_set_option(m.h, "kseg", kseg)
+    u64 = I.u_wave(X)
+    f64 = torch.sin(3 * X[:, 1]) + X[:, 2]
+    mask = torch.empty_like(u64)
+    H.hhg_residual(m.h, 0, torch.ones_like(u64), torch.zeros_like(u64), mask, 0)
+    u64 *= mask
+    f64 *= mask
+    del X
+    for dt in (H.HHG_F64, H.HHG_F32, H.HHG_F32_KBF16):
+        u = u64 if dt == H.HHG_F64 else u64.float()
+        f = f64 if dt == H.HHG_F64 else f64.float()
+        y = torch.full_like(u, float("nan"))
+        r = torch.full_like(u, float("nan"))
+        H.hhg_apply_scaled(m.h, 0, u, y, dt)
+        H.hhg_residual(m.h, 0, f, u, r, dt)
+        assert not bool(torch.isnan(y).any()) and not bool(torch.isnan(r).any())
+        assert torch.equal(r, f - y), (dt, float((r - (f - y)).abs().max()))
+    m.close()
