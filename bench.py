@@ -833,6 +833,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the 6-tet cube, tables, batch and learned sections")
+    ap.add_argument("--no-tune", action="store_true", help="skip the work-list autotuner (default segmentation)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the multigrid tables (scalar and tensor)")
     ap.add_argument("--only-learned", action="store_true",
@@ -865,7 +866,7 @@ def main():
     setup_s = time.perf_counter() - t_setup
     y = torch.empty_like(u)
     DT = H.HHG_F32_KBF16
-    tune = H.hhg_autotune(m.h, DT)
+    tune = None if args.no_tune else H.hhg_autotune(m.h, DT)
     for _ in range(max(3, args.warmup)):
         H.hhg_apply_scaled(m.h, 0, u, y, DT, stream)
     torch.cuda.synchronize()
@@ -896,9 +897,10 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
             "peak_source": f"{src} hbm_gbs (burst)",
-            "kernel": "march_kernel<float,__nv_bfloat16,2,APPLY> (volume rows) + boundary_only_kernel (interface "
-                      "rows, concurrent on a forked stream); achieved = algorithmic bytes / CUDA-event time of the "
-                      "pair on the caller's stream",
+            "kernel": "volume kernel chosen by the autotuner (march_kernel<float,__nv_bfloat16,APPLY>, the column "
+                      "march, or scaled_op_kernel, the tile march) + boundary_only_kernel (interface rows, concurrent on "
+                      "a forked stream); achieved = algorithmic bytes / CUDA-event time of the pair on the caller's "
+                      "stream",
             "algorithmic_bytes_per_launch": algo_bytes, "algorithmic_bytes_per_unknown": 10,
             "stored_node_bytes_fraction": 10 * n / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
 
@@ -917,10 +919,12 @@ def main():
 
     # the other operators on the same workload: FP32 k, the nodal-integration
     # apply (the paper's cost comparison), FP64 against the FP64-ALU peak
-    tune32 = H.hhg_autotune(m.h, H.HHG_F32)
+    tune32 = None if args.no_tune else H.hhg_autotune(m.h, H.HHG_F32)
     f32_ms = events_ms(torch, stream, flush, lambda: H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32, stream), 10)
-    H.hhg_set_option(m.h, "kseg", tune["kseg"])
-    H.hhg_set_option(m.h, "korder", tune["korder"])
+    if tune is not None:
+        H.hhg_set_option(m.h, "vkernel", tune["vkernel"])
+        H.hhg_set_option(m.h, "kseg", tune["kseg"])
+        H.hhg_set_option(m.h, "korder", tune["korder"])
     nodal_ms = events_ms(torch, stream, flush, lambda: H.hhg_apply_nodal(m.h, 0, u, y, DT, stream), 10)
     alu = alu_peaks(H, torch, stream)
     nodal_tf = 211 * unknowns / (nodal_ms * 1e-3) / 1e12

@@ -219,9 +219,11 @@ int hhg_apply_nodal(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, in
  * HHG_F32. */
 int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int dtype, void* stream);
 
-/* Autotune the volume work list for `dtype` (not part of the method): time
- * the scaled apply on depth 0 for every candidate k-segment length (16, 32,
- * 64) and work order (0, 1), keep the fastest on the mesh, and report it.
+/* Autotune the volume work for `dtype` (not part of the method): time the
+ * scaled apply on depth 0 for every candidate volume kernel (the "vkernel"
+ * option: 1 column march, 0 tile march), k-segment length (16, 32, 64) and
+ * work order (0, 1), keep the fastest on the mesh, and report its kseg and
+ * korder (the kernel: hhg_get_option "vkernel").
  * cache_path (may be NULL): a text file of earlier results keyed by the mesh
  * shape and dtype; a hit skips the search, a miss appends the new result.
  * Synchronous.  kseg, korder, best_ms may be NULL (best_ms < 0 on a hit). */

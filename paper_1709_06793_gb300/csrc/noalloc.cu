@@ -13,8 +13,7 @@
 // holds it (kNoAllocBytes) until the process exits.  Host code must not pass
 // the array's name to a kernel (on the host the name is only a stand-in for
 // the device symbol, not a device address); it looks the device address up
-// once per device with cudaGetSymbolAddress and passes that pointer.
-#include <mutex>
+// with cudaGetSymbolAddress on every call and passes that pointer.
 #include <new>
 
 #include "hhg_internal.h"
@@ -26,25 +25,14 @@ constexpr size_t kNoAllocBytes = 16u << 20;  // 16 MiB: 2M FP64 or 4M FP32 entri
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up on the
-// first call per device).
+// Device address of the scratch array in the current context, looked up on
+// every call (a cached address would outlive a device reset)
 void* noalloc_scratch() {
-  int dev = 0;
-  HHG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) throw Error{HHG_ERR_ARG, "device index out of range"};
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      throw Error{HHG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
-    g_noalloc_ptr[dev] = p;
-  }
-  return g_noalloc_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    throw Error{HHG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+  return p;
 }
 }  // namespace
 

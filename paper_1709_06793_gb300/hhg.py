@@ -224,7 +224,7 @@ def hhg_autotune(mesh, dtype, cache_path=None, stream=None):
     ks, ko, ms = C.c_int(), C.c_int(), C.c_double()
     _check(_lib.hhg_autotune(mesh, dtype, cache_path.encode() if cache_path else None, C.byref(ks), C.byref(ko),
                              C.byref(ms), _stream(stream)))
-    return {"kseg": ks.value, "korder": ko.value, "best_ms": ms.value}
+    return {"kseg": ks.value, "korder": ko.value, "vkernel": int(hhg_get_option(mesh, "vkernel")), "best_ms": ms.value}
 
 
 def hhg_residual(mesh, depth, f, u, r, dtype, stream=None):
