@@ -60,10 +60,18 @@ C2_WORKLOAD = "unit cube, 6 Kuhn macro-tets, level 8 (257 nodes/edge), k=exp(sin
 CPU_LEVEL = 4  # the oracle's apply sample of the headline workload (14,911 unknowns)
 CPU_SOLVE_LEVEL = 5  # its GMG-CG sample (125,055 unknowns)
 
-# ncu DRAM traffic (read + write bytes) of one scaled apply per stored node,
-# with the hash of the kernel sources it was measured on; the figure is
-# dropped (null) as soon as those sources change.  Keyed by dtype.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (read + write bytes) of one scaled apply, with the hash of
+# the kernel sources it was measured on; the figure is dropped (null) as soon
+# as those sources change.  Captured on the 24-tet cube at level 8 (68,693,016
+# stored nodes; the level-9 workload is too large to capture, so it is scaled
+# kernel by kernel: the volume kernel by stored nodes, the interface kernel by
+# interface copies), one kernel per ncu call (profiles/apply_bf16k_cube24_l8_traffic.md).
+NCU_TRAFFIC = {
+    "bf16k_cube24": {"sha": "edf6519a5d4ab118", "volume_bytes_per_node": (605144064 + 275206144) / 68693016,
+                     "interface_bytes_per_copy": (307726848 + 41057024) / (24 * (257 * 258 * 259 // 6 - 255 * 254 * 253 // 6)),
+                     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 24-tet cube level 8, march_kernel and "
+                               "boundary_only_kernel captured separately, scaled to this workload per kernel unit"},
+}
 
 
 def _code_only(src):
@@ -83,11 +91,18 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic(dtype_name, n_stored):
+def interface_copies(T, level):
+    """Stored copies on macro faces, edges and vertices: every tet's nodes
+    minus its interior nodes."""
+    N = 1 << level
+    return len(T) * ((N + 1) * (N + 2) * (N + 3) // 6 - (N - 1) * (N - 2) * (N - 3) // 6)
+
+
+def _traffic(dtype_name, n_stored, n_copies):
     rec = NCU_TRAFFIC.get(dtype_name)
     if not rec or rec["sha"] != _kernel_sha():
         return None, None
-    return rec["bytes_per_node"] * n_stored, rec["source"]
+    return rec["volume_bytes_per_node"] * n_stored + rec["interface_bytes_per_copy"] * n_copies, rec["source"]
 
 
 def _peaks():
@@ -792,7 +807,7 @@ def c2_section(H, I, torch, stream, flush, steps):
     volface_ms = events_ms(torch, stream, flush, lambda: H.hhg_apply_volface(m.h, 0, u, y, H.HHG_F32, stream), 10)
     peaks, src = _peaks()
     algo = 12 * unknowns
-    traffic, tsrc = _traffic("f32_kuhn_cube_l8", n)
+    traffic, tsrc = _traffic("f32_kuhn_cube", n, interface_copies(T, C2_LEVEL))
     out = {"workload": C2_WORKLOAD, "unknowns": unknowns, "stored_nodes": n, "autotune": tune,
            "apply_ms": ms, "apply_gdofs": unknowns / (ms * 1e-3) / 1e9,
            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
@@ -893,7 +908,7 @@ def main():
     peaks, src = _peaks()
     algo_bytes = 10 * unknowns  # read u (FP32), k (BF16); write y (FP32): every unknown once
     achieved = algo_bytes / (ms * 1e-3) / 1e9
-    traffic, tsrc = _traffic("bf16k_cube24", n)
+    traffic, tsrc = _traffic("bf16k_cube24", n, interface_copies(T, args.level))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
             "peak_source": f"{src} hbm_gbs (burst)",

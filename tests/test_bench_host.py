@@ -49,3 +49,12 @@ def test_reference_arm_line_states_the_sample_it_timed(monkeypatch, capsys):
     assert line["config"]["processes"] == line["cpu_baseline"]["cores"] == bench.host_info()["nproc"]
     assert "level 2" in line["config"]["workload"] and "level 9" not in line["config"]["workload"]
     assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_interface_copies_count_the_stored_face_nodes():
+    """Stored nodes minus interior nodes, per tet: at level 1 every node of a
+    tet is on its boundary; a tet at level 2 has one interior node."""
+    from paper_1709_06793_gb300 import inputs as I
+    _, T = I.cube24()
+    assert bench.interface_copies(T, 1) == 24 * 10
+    assert bench.interface_copies(T, 2) == 24 * (35 - 1)
