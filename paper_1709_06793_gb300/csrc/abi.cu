@@ -214,7 +214,6 @@ int hhg_apply_tensor(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, i
     need_vec(u_dev, "u_dev");
     need_vec(y_dev, "y_dev");
     if (u_dev == y_dev) throw Error{HHG_ERR_ARG, "u_dev and y_dev must not overlap"};
-    const int pr = dtype == HHG_F64 ? 0 : 1;
     OpArgs a{u_dev, nullptr, y_dev, nullptr, nullptr, 0, 0, 0, 0};
     launch_tensor_op(m, depth, dtype, OP_APPLY, a, (cudaStream_t)stream);
   });

@@ -142,11 +142,16 @@ struct Depth {
   float* km32 = nullptr;
   const double* tsten64 = nullptr;
   const float* tsten32 = nullptr;
-  // per-direction node weights of the tensor operator's volume rows
-  // (B_d = sum_m c^m_d k_m for the 7 positive directions d of the volume
-  // stencil; direction major: 7 x n_stored), set with the tensor coefficient
+  // edge weights of the tensor operator's volume rows (W_e(x) = sum_m
+  // c^m_e (k_m(x) + k_m(x+w_e)) for the 7 positive directions e of the volume
+  // stencil; direction major, stride n_stored rounded up to 16), and of its
+  // interface rows (per boundary copy and each of the 14 directions, with
+  // the stencils of the copy's primitive; direction major, stride the copy
+  // count), set with the tensor coefficient
   double* tb64 = nullptr;
   float* tb32 = nullptr;
+  double* twb64 = nullptr;
+  float* twb32 = nullptr;
   double* k64 = nullptr;
   float* k32 = nullptr;
   __nv_bfloat16* k16 = nullptr;
@@ -306,6 +311,7 @@ void launch_volface_op(const Mesh& m, int depth, int dtype, OpMode mode, const O
 void launch_nodal_dinv(const Mesh& m, int depth, int dtype, void* dinv, cudaStream_t s);
 // scaled operator of the tensor coefficient (M = 6) in the modes above
 void compute_tensor_weights(Mesh& m, cudaStream_t s);
+void init_tensor_configs();  // shared-memory limits of the tensor march kernels
 void launch_tensor_op(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a,
                       cudaStream_t s);
 void ensure_tensor_stencils(Mesh& m);

@@ -34,14 +34,6 @@ __device__ __forceinline__ int row_start(int N, int q, int j) {
   return pl + j * (M + 1) - j * (j - 1) / 2;
 }
 
-template <class E>
-__device__ __forceinline__ double as_f64(E v) {
-  return (double)v;
-}
-template <>
-__device__ __forceinline__ double as_f64<__nv_bfloat16>(__nv_bfloat16 v) {
-  return (double)__bfloat162float(v);
-}
 template <class T, class E>
 __device__ __forceinline__ T as_t(E v) {
   if constexpr (sizeof(E) == 2)

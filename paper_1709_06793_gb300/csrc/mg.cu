@@ -114,6 +114,7 @@ void set_tensor_coefficient(Mesh& m, const double* K6, cudaStream_t s) {
                                          reinterpret_cast<K6f*>(C.km32));
     HHG_CUDA(cudaGetLastError());
   }
+  init_tensor_configs();
   compute_tensor_weights(m, s);
   m.tensor_set = true;
   for (int t = 0; t < 4; ++t) m.cinv_ready[3][t] = false;

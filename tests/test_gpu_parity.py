@@ -476,8 +476,13 @@ def test_mg_solver_rejects_operator_outside_mg_mode(H):
     c.m.close()
 
 
+# the tensor operator's column march: several column tiles (30 wide) and row
+# tiles (16 high) per macro-tet with ragged last tiles at levels 5 and 6
+TENSOR_MESHES = {**MESHES, "cube12_l5": (I.cube12, 5, 2, I.k_cube), "kuhn_cube_l6": (I.kuhn_cube, 6, 2, I.k_cube)}
+
+
 def _tensor_case(H, name):
-    mesh, level, coarsest, kf = MESHES[name]
+    mesh, level, coarsest, kf = TENSOR_MESHES[name]
     V, T = mesh()
     c = Case(H, V, T, level, coarsest, kf)
     K6 = np.ascontiguousarray(I.K_tensor(c.xyz).T)  # (6, n_stored)
@@ -486,7 +491,7 @@ def _tensor_case(H, name):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
-@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3"])
+@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3", "cube12_l5", "kuhn_cube_l6"])
 def test_tensor_apply_parity(H, name, dtype):
     """Scaled operator of the tensor coefficient (M = 6) against the oracle's
     element loop over the six terms; FP32 on FP32-rounded inputs."""
@@ -507,7 +512,7 @@ def test_tensor_apply_parity(H, name, dtype):
     c.m.close()
 
 
-@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3"])
+@pytest.mark.parametrize("name", ["kuhn_cube_l4", "cube12_l3", "cube12_l5"])
 def test_tensor_mg_solver_parity(H, name):
     c, (V, T, level, coarsest) = _tensor_case(H, name)
     Ho = O.Hierarchy(V, T, level, coarsest, K_func=I.K_tensor)
