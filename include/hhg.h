@@ -221,7 +221,8 @@ int hhg_apply_mass(hhg_mesh mesh, int depth, const void* u_dev, void* y_dev, int
 
 /* Autotune the volume work for `dtype` (not part of the method): time the
  * scaled apply on depth 0 for every candidate volume kernel (the "vkernel"
- * option: 1 column march, 0 tile march), k-segment length (16, 32, 64) and
+ * option: 1 column march, 2 column march with two column sets per lane --
+ * FP32 dtypes only --, 0 tile march), k-segment length (16, 32, 64) and
  * work order (0, 1), keep the fastest on the mesh, and report its kseg and
  * korder (the kernel: hhg_get_option "vkernel").
  * cache_path (may be NULL): a text file of earlier results keyed by the mesh
@@ -361,7 +362,9 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
  * part of the method): "kseg" planes per volume work item of the k-march and
  * "korder" (0: longest item first, 1: items ordered by plane window) -- both
  * rebuild the work lists and synchronise the device --, "vkernel" (1: the
- * column-march volume kernel, 0: the tile-march one), "cheb_degree",
+ * column-march volume kernel, 2: the same with two column sets per lane in
+ * packed FP32x2 arithmetic for the FP32 dtypes, FP64 running as 1; 0: the
+ * tile-march one), "cheb_degree",
  * "cheb_lo", "cheb_hi" (Chebyshev interval as fractions of lambda_max) and
  * "power_its" (lambda_max estimate).  Unknown keys or out-of-range values:
  * HHG_ERR_ARG. */

@@ -417,7 +417,7 @@ int hhg_set_option(hhg_mesh mesh, const char* key, double value) {
         for (int t = 0; t < 4; ++t) m.cinv_ready[o][t] = false;
       for (Depth& D : m.depth) D.lam = 0.0;
     } else if (k == "vkernel") {
-      if (value != 0 && value != 1) throw Error{HHG_ERR_ARG, "vkernel must be 0 or 1"};
+      if (value != 0 && value != 1 && value != 2) throw Error{HHG_ERR_ARG, "vkernel must be 0, 1 or 2"};
       m.vkernel = (int)value;
     } else if (k == "cheb_degree") {
       if (value < 1 || value > 16) throw Error{HHG_ERR_ARG, "cheb_degree must be in [1, 16]"};

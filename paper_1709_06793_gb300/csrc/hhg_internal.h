@@ -74,11 +74,11 @@ struct DepthDev {
   const int4* items;     // volume work: (tile = slot<<20 | j0<<10 | i0, k0, k1, -) per warp item
   int n_items;           // items of all active tets
   int n_items_nc;        // items of tets above the coarsest level (prefix)
-  const int4* mitems;    // column-march work: (pair, i0 | j0<<16, k0, k1) per warp item
-  const int2* pairs;     // (slot a, slot b or -1): pairs of same-level tets, then every slot alone
-  int n_mitems;          // items over the pairs (packed FP32x2 kernels)
+  const int4* mitems;    // column-march work, 60-column tiles: (slot index, i0 | j0<<16, k0, k1) per block item
+  const int2* pairs;     // (slot, -1) per active slot
+  int n_mitems;          // items of the two-column-set (FP32x2) march
   int n_mitems_nc;       // of those, items of tets above the coarsest level (prefix)
-  const int4* sitems;    // the same over single tets (FP64 kernels)
+  const int4* sitems;    // the same over 30-column tiles (one column set per lane)
   int n_sitems;
   int n_sitems_nc;
   const int* bstart;     // boundary unique nodes: copies bstart[b]..bstart[b+1]
@@ -229,7 +229,8 @@ struct Mesh {
   double cheb_lo = 0.3, cheb_hi = 1.1;
   int power_its = 15;
   int kseg = 32;                  // planes per volume work item (k-march segment)
-  int vkernel = 1;                // volume kernel: 1 column march (march.cu), 0 tile march (apply.cu)
+  int vkernel = 1;                // volume kernel: 1 column march (march.cu), 2 the same with two column
+                                  // sets per lane in FP32, 0 tile march (apply.cu)
   bool kappa = false;             // scaled operator with k_min on gray directions (eq. "defKmin", kappa.cu)
   int korder = 0;                 // work order: 0 longest first, 1 by plane window, 2 j-stacked quads by window
   // learned smoother state (opaque)

@@ -28,6 +28,12 @@
 // commit group per plane keeps S-1 planes in flight, and the block waits for
 // its plane's group (cp.async.wait_group + __syncthreads).  No spin loop
 // waits on memory.
+//
+// FP32 also runs with two column sets per lane (P = 2): lane L holds columns
+// i0-1+L and i0+29+L of a 60-column tile, and the flux and row arithmetic
+// of both columns is one packed FP32x2 instruction (add / mul / fma .f32x2),
+// which halves the issued arithmetic per node; copies, shared loads and
+// shuffles stay per column, the row addressing is shared by both.
 #include <algorithm>
 
 #include "hhg_internal.h"
@@ -71,15 +77,18 @@ constexpr int kRowsW = 4;                    // owned rows per warp
 constexpr int kRowsM = kRowsW + 2;           // rows a warp reads
 constexpr int kRowsB = kWarps * kRowsW + 2;  // rows staged per plane (j0-1 .. j0+16)
 constexpr int kRowsF = kWarps * kRowsW;      // f rows staged per plane (j0 .. j0+15)
-constexpr int kCols = 30;                    // owned columns per tile
+constexpr int kCols = 30;                    // owned columns per tile (per column set)
+constexpr int kSet = 30;                     // column distance of a lane's two column sets
 constexpr int kThreads = kWarps * 32;
 
-template <class T, class KT, int MODE>
+template <class T, class KT, int MODE, int P = 1>
 struct Geo {
   static constexpr int VU = 16 / (int)sizeof(T);
   static constexpr int VK = 16 / (int)sizeof(KT);
-  static constexpr int WU = 32 + VU;  // elements of a staged u / f row (one 16-byte chunk of head room)
-  static constexpr int WK = 32 + VK;
+  static constexpr int COLS = 32 + kSet * (P - 1);  // columns a warp reads
+  // elements of a staged u / f row (whole chunks, one chunk of head room)
+  static constexpr int WU = (COLS + VU - 1) / VU * VU + VU;
+  static constexpr int WK = (COLS + VK - 1) / VK * VK + VK;
   static constexpr int RU = WU * (int)sizeof(T);
   static constexpr int RK = WK * (int)sizeof(KT);
   static constexpr bool F = MODE == OP_RESID || MODE == OP_JACOBI || MODE == OP_CHEB;
@@ -92,6 +101,7 @@ struct Geo {
   static constexpr int SK = (kRowsB * CHK + kThreads - 1) / kThreads;  // k
   static constexpr int SF = F ? (kRowsF * CHU + kThreads - 1) / kThreads : 0;  // f
   static constexpr int S = sizeof(T) == 8 ? 4 : 5;  // stages (S-1 planes in flight)
+  static constexpr int REACH = (WU > WK ? WU : WK) + 16;  // elements a row's chunks reach past its start
   static constexpr int SMEM = S * SB;
   static_assert(RU % 16 == 0 && RK % 16 == 0, "staged rows must keep 16-byte alignment");
 };
@@ -132,15 +142,63 @@ template <class T>
 __device__ __forceinline__ T shup(T a) {
   return __shfl_up_sync(0xffffffffu, a, 1);
 }
-template <class T>
-__device__ __forceinline__ T flux(T ua, T ka, T ub, T kb) {
-  return (ka + kb) * (ub - ua);
+// The flux product is rounded on its own (no contraction into a following
+// add), so the one- and two-column-set kernels round every node alike.
+__device__ __forceinline__ float flux(float ua, float ka, float ub, float kb) {
+  return __fmul_rn(ka + kb, ub - ua);
+}
+__device__ __forceinline__ double flux(double ua, double ka, double ub, double kb) {
+  return __dmul_rn(ka + kb, ub - ua);
 }
 
-template <class T, class KT, int MODE>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI || MODE == OP_CHEB ? 2 : 3)
+// packed pairs (two column sets per lane): one FP32x2 instruction per
+// operation, each component rounded as the scalar operation would be
+// (a - b as fma(b, -1, a): the product is exact, one rounding of a - b)
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2& operator+=(float2& a, float2 b) { return a = a + b; }
+__device__ __forceinline__ float2& operator-=(float2& a, float2 b) { return a = a - b; }
+using ::fma;
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 flux(float2 ua, float2 ka, float2 ub, float2 kb) { return (ka + kb) * (ub - ua); }
+template <>
+__device__ __forceinline__ float2 shdown<float2>(float2 a) {
+  return make_float2(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
+}
+template <>
+__device__ __forceinline__ float2 shup<float2>(float2 a) {
+  return make_float2(__shfl_up_sync(0xffffffffu, a.x, 1), __shfl_up_sync(0xffffffffu, a.y, 1));
+}
+
+// value type of P column sets per lane
+template <class T, int P>
+struct Lanes {
+  using V = T;
+  static __device__ __forceinline__ V splat(T x) { return x; }
+  static __device__ __forceinline__ T comp(V v, int) { return v; }
+  template <class E>
+  static __device__ __forceinline__ V ld(const E* row, int i) {
+    return to_t<T, E>(row[i]);
+  }
+};
+template <>
+struct Lanes<float, 2> {
+  using V = float2;
+  static __device__ __forceinline__ V splat(float x) { return make_float2(x, x); }
+  static __device__ __forceinline__ float comp(V v, int h) { return h ? v.y : v.x; }
+  template <class E>
+  static __device__ __forceinline__ V ld(const E* row, int i) {
+    return make_float2(to_f32(row[i]), to_f32(row[i + kSet]));
+  }
+};
+
+template <class T, class KT, int MODE, int P>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI || MODE == OP_CHEB || P == 2 ? 2 : 3)
     march_kernel(DepthDev D, const T* __restrict__ sten, MarchPtrs p, int n_items) {
-  using G = Geo<T, KT, MODE>;
+  using G = Geo<T, KT, MODE, P>;
+  using L = Lanes<T, P>;
+  using V = typename L::V;
   constexpr int S = G::S;
   constexpr bool DIAG = MODE == OP_JACOBI || MODE == OP_CHEB || MODE == OP_DIAG;
   constexpr int EU = (int)sizeof(T), EK = (int)sizeof(KT);
@@ -170,20 +228,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
   }
   const bool own_lane = lane >= 1 && lane <= kCols;
 
+  const int4* __restrict__ items = P == 2 ? D.mitems : D.sitems;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int4 item = D.sitems[it];
+    const int4 item = items[it];
     const int slot = D.pairs[item.x].x;
     const TetDev td = D.tets[slot];
     const int N = td.N;
     const int i0 = item.y & 0xffff, j0 = item.y >> 16, k0 = item.z, k1 = item.w;
     const int jw = j0 + kRowsW * w;  // first owned row of this warp
-    T c[7];
+    V c[7];
+    T cs = 0;
 #pragma unroll
-    for (int e = 0; e < 7; ++e) c[e] = sten[slot * 16 * kNDir + e];
-    T csum = c[0];
-#pragma unroll
-    for (int e = 1; e < 7; ++e) csum += c[e];
-    csum += csum;
+    for (int e = 0; e < 7; ++e) {
+      const T ce = sten[slot * 16 * kNDir + e];
+      c[e] = L::splat(ce);
+      cs = e ? cs + ce : ce;
+    }
+    const V csum = L::splat(cs + cs);
     const int q_first = k0 - 1;
 
     // Element tb + r is node (i0-1, row offset r) of the tet.  Its 16-byte
@@ -192,8 +253,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
     const long long tb = td.base + i0 - 1;
     const int tl = (int)(tb & 15);
     // every chunk of the tile lies before the end of the arrays (then no copy
-    // needs clipping): the tet's nodes + 48 elements of head room
-    const long long reach = tb + (long long)(N + 1) * (N + 2) * (N + 3) / 6 + 48;
+    // needs clipping): the tet's nodes + a staged row's width + 16 elements
+    const long long reach = tb + (long long)(N + 1) * (N + 2) * (N + 3) / 6 + G::REACH;
     const bool inside = reach <= p.lim_u && reach <= p.lim_k;
     const unsigned char* bu = reinterpret_cast<const unsigned char*>(static_cast<const T*>(p.u) + (tb - tl));
     const unsigned char* bk = reinterpret_cast<const unsigned char*>(static_cast<const KT*>(p.k) + (tb - tl));
@@ -263,10 +324,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
     for (int t = 0; t < S - 1; ++t) issue();
 
     // thread state
-    T xu[2][kRowsM], xk[2][kRowsM];  // planes (two buffers, roles alternate)
+    V xu[2][kRowsM], xk[2][kRowsM];  // planes (two buffers, roles alternate)
     int rs[kRowsM];                  // row offsets (rows jw-1+m) of the plane being computed
-    T F2p[4], F4c[4], F5c[4], F6p[5];  // carried fluxes
-    T kp[5], dkp[4];                   // plane q-1: own k (rows 1..5), right k (rows 1..4)
+    V F2p[4], F4c[4], F5c[4], F6p[5];  // carried fluxes
+    V kp[5], dkp[4];                   // plane q-1: own k (rows 1..5), right k (rows 1..4)
 #pragma unroll
     for (int m = 0; m < kRowsM; ++m) rs[m] = row_offset(N, q_first, jw - 1 + m);
     // row m of plane q+1 starts at rs[m] + dlt(q) - m
@@ -284,8 +345,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
       for (int m = 0; m < kRowsM; ++m) {
         const int t = tl + rs[m] + dl - dm * m;
         const int r = kRowsW * w + m;
-        xu[b][m] = reinterpret_cast<const T*>(sb + r * G::RU)[(t & (G::VU - 1)) + lane];
-        xk[b][m] = to_t<T, KT>(reinterpret_cast<const KT*>(sb + G::OFF_K + r * G::RK)[(t & (G::VK - 1)) + lane]);
+        xu[b][m] = L::ld(reinterpret_cast<const T*>(sb + r * G::RU), (t & (G::VU - 1)) + lane);
+        xk[b][m] = L::ld(reinterpret_cast<const KT*>(sb + G::OFF_K + r * G::RK), (t & (G::VK - 1)) + lane);
       }
     };
     auto advance_rows = [&](int dl) {
@@ -293,9 +354,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
       for (int m = 0; m < kRowsM; ++m) rs[m] += dl - m;
     };
     // f at owned row m of the plane being computed (carried by the stage of the next plane)
-    auto f_at = [&](int m) -> T {
+    auto f_at = [&](int m) -> V {
       const int t = tl + rs[m];
-      return reinterpret_cast<const T*>(sb_last + G::OFF_F + (kRowsW * w + m - 1) * G::RU)[(t & (G::VU - 1)) + lane];
+      return L::ld(reinterpret_cast<const T*>(sb_last + G::OFF_F + (kRowsW * w + m - 1) * G::RU), (t & (G::VU - 1)) + lane);
     };
     T* __restrict__ po = static_cast<T*>(p.out) + tb + lane;
 
@@ -311,8 +372,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
     // right neighbours (lane L+1) are shuffled where they are used
 #pragma unroll
     for (int m = 1; m <= 4; ++m) {
-      const T d0u = shdown(xu[0][m]), d0k = shdown(xk[0][m]);
-      const T d1u = shdown(xu[1][m - 1]), d1k = shdown(xk[1][m - 1]);
+      const V d0u = shdown(xu[0][m]), d0k = shdown(xk[0][m]);
+      const V d1u = shdown(xu[1][m - 1]), d1k = shdown(xk[1][m - 1]);
       F2p[m - 1] = flux(xu[0][m], xk[0][m], xu[1][m], xk[1][m]);
       F6p[m - 1] = flux(xu[0][m], xk[0][m], d1u, d1k);
       F4c[m - 1] = flux(xu[1][m], xk[1][m], d0u, d0k);
@@ -332,42 +393,42 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
       consume(b, dl, 1);
       // row m of this lane holds a volume node iff m <= mlim
       const int mlim = N - q - (i0 - 1 + lane) - (jw - 1) - 1;
-      T F1prev = flux(xu[a][0], xk[a][0], xu[a][1], xk[a][1]);
-      T F5prev = flux(xu[b][0], xk[b][0], xu[a][1], xk[a][1]);
-      T dak = shdown(xk[a][0]);  // k at (i+1, row m-1) of plane q
-      T F3cur = flux(xu[a][1], xk[a][1], shdown(xu[a][0]), dak);
+      V F1prev = flux(xu[a][0], xk[a][0], xu[a][1], xk[a][1]);
+      V F5prev = flux(xu[b][0], xk[b][0], xu[a][1], xk[a][1]);
+      V dak = shdown(xk[a][0]);  // k at (i+1, row m-1) of plane q
+      V F3cur = flux(xu[a][1], xk[a][1], shdown(xu[a][0]), dak);
 #pragma unroll
       for (int m = 1; m <= 4; ++m) {
-        const T dau = shdown(xu[a][m]), dakm = shdown(xk[a][m]);          // (i+1, row m), plane q
-        const T dbu = shdown(xu[b][m - 1]), dbk = shdown(xk[b][m - 1]);  // (i+1, row m-1), plane q+1
-        const T F0 = flux(xu[a][m], xk[a][m], dau, dakm);
-        const T F1 = flux(xu[a][m], xk[a][m], xu[a][m + 1], xk[a][m + 1]);
-        const T F2 = flux(xu[a][m], xk[a][m], xu[b][m], xk[b][m]);
-        const T F3n = flux(xu[a][m + 1], xk[a][m + 1], dau, dakm);
-        const T F6 = flux(xu[a][m], xk[a][m], dbu, dbk);
-        const T F4n = flux(xu[b][m], xk[b][m], dau, dakm);
-        const T F5n = flux(xu[b][m], xk[b][m], xu[a][m + 1], xk[a][m + 1]);
-        const T t0 = c[0] * F0;
-        T H = fma(c[3], F3n, t0);
+        const V dau = shdown(xu[a][m]), dakm = shdown(xk[a][m]);          // (i+1, row m), plane q
+        const V dbu = shdown(xu[b][m - 1]), dbk = shdown(xk[b][m - 1]);  // (i+1, row m-1), plane q+1
+        const V F0 = flux(xu[a][m], xk[a][m], dau, dakm);
+        const V F1 = flux(xu[a][m], xk[a][m], xu[a][m + 1], xk[a][m + 1]);
+        const V F2 = flux(xu[a][m], xk[a][m], xu[b][m], xk[b][m]);
+        const V F3n = flux(xu[a][m + 1], xk[a][m + 1], dau, dakm);
+        const V F6 = flux(xu[a][m], xk[a][m], dbu, dbk);
+        const V F4n = flux(xu[b][m], xk[b][m], dau, dakm);
+        const V F5n = flux(xu[b][m], xk[b][m], xu[a][m + 1], xk[a][m + 1]);
+        const V t0 = c[0] * F0;
+        V H = fma(c[3], F3n, t0);
         H = fma(c[4], F4n, H);
         H = fma(c[6], F6p[m], H);  // F6p[m] holds row m+1
-        T y = fma(c[1], F1 - F1prev, t0);
+        V y = fma(c[1], F1 - F1prev, t0);
         y = fma(c[2], F2 - F2p[m - 1], y);
         y = fma(c[3], F3cur, y);
         y = fma(c[4], F4c[m - 1], y);
         y = fma(c[5], F5c[m - 1] - F5prev, y);
         y = fma(c[6], F6, y);
         y -= shup(H);
-        T dg = y;
+        V dg = y;
         if (DIAG) {
-          T sk = c[0] * dakm;
+          V sk = c[0] * dakm;
           sk = fma(c[1], xk[a][m + 1] + xk[a][m - 1], sk);
           sk = fma(c[2], xk[b][m] + kp[m - 1], sk);
           sk = fma(c[3], dak, sk);
           sk = fma(c[4], dkp[m - 1], sk);
           sk = fma(c[5], kp[m] + xk[b][m - 1], sk);
           sk = fma(c[6], dbk, sk);
-          T hd = c[0] * xk[a][m];
+          V hd = c[0] * xk[a][m];
           hd = fma(c[3], xk[a][m + 1], hd);
           hd = fma(c[4], xk[b][m], hd);
           hd = fma(c[6], kp[m], hd);
@@ -383,23 +444,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
         F3cur = F3n;
         if (DIAG) dkp[m - 1] = dakm;
         dak = dakm;
-        // epilogue: owned lanes, volume nodes only
-        if (own_lane && m <= mlim) {
-          T* o = po + rs[m];
-          if (MODE == OP_APPLY) {
-            *o = y;
-          } else if (MODE == OP_RESID) {
-            *o = f_at(m) - y;
-          } else if (MODE == OP_JACOBI) {
-            *o = xu[a][m] + qdiv((T)p.omega * (f_at(m) - y), -dg);
-          } else if (MODE == OP_CHEB) {
-            const long long idx = o - static_cast<T*>(p.out);
-            const T prev = p.ca != 0.0 ? (T)p.ca * __ldg(static_cast<const T*>(p.d_in) + idx) : (T)0;
-            const T dn = prev + (T)p.cb * (f_at(m) - y) / -dg;
-            static_cast<T*>(p.d_out)[idx] = dn;
-            *o = xu[a][m] + dn;
-          } else {  // OP_DIAG
-            *o = -dg;
+        // epilogue: owned lanes, volume nodes only (column set h at +30 h)
+        if (own_lane) {
+          V fv;
+          if (G::F) fv = f_at(m);
+#pragma unroll
+          for (int h = 0; h < P; ++h) {
+            if (m > mlim - kSet * h) continue;
+            T* o = po + rs[m] + kSet * h;
+            const T yv = L::comp(y, h);
+            if (MODE == OP_APPLY) {
+              *o = yv;
+            } else if (MODE == OP_RESID) {
+              *o = L::comp(fv, h) - yv;
+            } else if (MODE == OP_JACOBI) {
+              *o = L::comp(xu[a][m], h) + qdiv((T)p.omega * (L::comp(fv, h) - yv), -L::comp(dg, h));
+            } else if (MODE == OP_CHEB) {
+              const long long idx = o - static_cast<T*>(p.out);
+              const T prev = p.ca != 0.0 ? (T)p.ca * __ldg(static_cast<const T*>(p.d_in) + idx) : (T)0;
+              const T dn = prev + (T)p.cb * (L::comp(fv, h) - yv) / -L::comp(dg, h);
+              static_cast<T*>(p.d_out)[idx] = dn;
+              *o = L::comp(xu[a][m], h) + dn;
+            } else {  // OP_DIAG
+              *o = -L::comp(dg, h);
+            }
           }
         }
       }
@@ -421,87 +489,100 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI 
   cp_wait<0>();
 }
 
-template <class T, class KT, int MODE>
+template <class T, class KT, int MODE, int P>
 int march_occupancy() {
   static int occ = 0;
   if (!occ) {
-    using G = Geo<T, KT, MODE>;
-    HHG_CUDA(cudaFuncSetAttribute(march_kernel<T, KT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
-    HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel<T, KT, MODE>, kThreads, G::SMEM));
+    using G = Geo<T, KT, MODE, P>;
+    HHG_CUDA(cudaFuncSetAttribute(march_kernel<T, KT, MODE, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    HHG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel<T, KT, MODE, P>, kThreads, G::SMEM));
     if (occ < 1) occ = 1;
   }
   return occ;
 }
 
-template <class T, class KT, int MODE>
+template <class T, class KT, int MODE, int P>
 void launch_t(const Mesh& m, int depth, const OpArgs& a, const void* kptr, long long lim_k, int n_items,
               cudaStream_t s) {
-  using G = Geo<T, KT, MODE>;
+  using G = Geo<T, KT, MODE, P>;
   const Depth& Dh = m.depth[depth];
-  const int occ = march_occupancy<T, KT, MODE>();
+  const int occ = march_occupancy<T, KT, MODE, P>();
   const int blocks = std::min(n_items, m.num_sms * occ);
   MarchPtrs p{a.u, kptr, a.f, a.out, a.d_in, a.d_out, a.omega, a.ca, a.cb, Dh.n_stored, lim_k};
   const T* sten = sizeof(T) == 8 ? reinterpret_cast<const T*>(Dh.dev.sten64) : reinterpret_cast<const T*>(Dh.dev.sten32);
-  march_kernel<T, KT, MODE><<<blocks, kThreads, G::SMEM, s>>>(Dh.dev, sten, p, n_items);
+  march_kernel<T, KT, MODE, P><<<blocks, kThreads, G::SMEM, s>>>(Dh.dev, sten, p, n_items);
   HHG_CUDA(cudaGetLastError());
 }
 
 template <int MODE>
-void launch_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, int n_items, cudaStream_t s) {
+void launch_mode(const Mesh& m, int depth, int dtype, const OpArgs& a, bool wide, cudaStream_t s) {
   const Depth& Dh = m.depth[depth];
+  const DepthDev& D = Dh.dev;
   const long long n = Dh.n_stored;
-  if (dtype == HHG_F64)
-    launch_t<double, double, MODE>(m, depth, a, Dh.k64, n + kCoefPad / 8, n_items, s);
-  else if (dtype == kF64KBF16)
-    launch_t<double, double, MODE>(m, depth, a, Dh.k16d, n + kCoefPad / 8, n_items, s);
-  else if (dtype == HHG_F32)
-    launch_t<float, float, MODE>(m, depth, a, Dh.k32, n + kCoefPad / 4, n_items, s);
-  else
-    launch_t<float, __nv_bfloat16, MODE>(m, depth, a, Dh.k16, n + kCoefPad / 2, n_items, s);
+  const int n1 = a.nc_only ? D.n_sitems_nc : D.n_sitems;
+  const int n2 = a.nc_only ? D.n_mitems_nc : D.n_mitems;
+  if (dtype == HHG_F64) {
+    if (n1) launch_t<double, double, MODE, 1>(m, depth, a, Dh.k64, n + kCoefPad / 8, n1, s);
+  } else if (dtype == kF64KBF16) {
+    if (n1) launch_t<double, double, MODE, 1>(m, depth, a, Dh.k16d, n + kCoefPad / 8, n1, s);
+  } else if (dtype == HHG_F32) {
+    if (wide) {
+      if (n2) launch_t<float, float, MODE, 2>(m, depth, a, Dh.k32, n + kCoefPad / 4, n2, s);
+    } else if (n1) {
+      launch_t<float, float, MODE, 1>(m, depth, a, Dh.k32, n + kCoefPad / 4, n1, s);
+    }
+  } else {
+    if (wide) {
+      if (n2) launch_t<float, __nv_bfloat16, MODE, 2>(m, depth, a, Dh.k16, n + kCoefPad / 2, n2, s);
+    } else if (n1) {
+      launch_t<float, __nv_bfloat16, MODE, 1>(m, depth, a, Dh.k16, n + kCoefPad / 2, n1, s);
+    }
+  }
 }
 
-template <class T, class KT>
+template <class T, class KT, int P>
 void init_t() {
-  march_occupancy<T, KT, OP_APPLY>();
-  march_occupancy<T, KT, OP_RESID>();
-  march_occupancy<T, KT, OP_JACOBI>();
-  march_occupancy<T, KT, OP_CHEB>();
-  march_occupancy<T, KT, OP_DIAG>();
+  march_occupancy<T, KT, OP_APPLY, P>();
+  march_occupancy<T, KT, OP_RESID, P>();
+  march_occupancy<T, KT, OP_JACOBI, P>();
+  march_occupancy<T, KT, OP_CHEB, P>();
+  march_occupancy<T, KT, OP_DIAG, P>();
 }
 
 }  // namespace
 
 void init_march_configs(int dtype) {
-  if (dtype == HHG_F64 || dtype == kF64KBF16)
-    init_t<double, double>();
-  else if (dtype == HHG_F32)
-    init_t<float, float>();
-  else
-    init_t<float, __nv_bfloat16>();
-}
-
-void launch_march(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
-  const DepthDev& D = m.depth[depth].dev;
-  const int n_items = a.nc_only ? D.n_sitems_nc : D.n_sitems;
-  if (n_items == 0) return;
-  switch (mode) {
-    case OP_APPLY: launch_mode<OP_APPLY>(m, depth, dtype, a, n_items, s); break;
-    case OP_RESID: launch_mode<OP_RESID>(m, depth, dtype, a, n_items, s); break;
-    case OP_JACOBI: launch_mode<OP_JACOBI>(m, depth, dtype, a, n_items, s); break;
-    case OP_CHEB: launch_mode<OP_CHEB>(m, depth, dtype, a, n_items, s); break;
-    case OP_DIAG: launch_mode<OP_DIAG>(m, depth, dtype, a, n_items, s); break;
+  if (dtype == HHG_F64 || dtype == kF64KBF16) {
+    init_t<double, double, 1>();
+  } else if (dtype == HHG_F32) {
+    init_t<float, float, 1>();
+    init_t<float, float, 2>();
+  } else {
+    init_t<float, __nv_bfloat16, 1>();
+    init_t<float, __nv_bfloat16, 2>();
   }
 }
 
-// Work list of the march: per tet (those above the coarsest level first),
-// tiles (i0, j0) of 30 columns x 16 rows, each tile's planes 1 ..
-// N-1-i0-j0 cut into segments of kseg planes; longest segment first within
-// a class (korder 1: by plane window).  kseg is halved (down to 4) while a
-// class would have fewer items than two per resident block.
-void build_march_items(const Mesh& m, Depth& D) {
+// vkernel 2: FP32 runs the march with two column sets per lane (FP64 keeps one)
+void launch_march(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
+  const bool wide = m.vkernel == 2;
+  switch (mode) {
+    case OP_APPLY: launch_mode<OP_APPLY>(m, depth, dtype, a, wide, s); break;
+    case OP_RESID: launch_mode<OP_RESID>(m, depth, dtype, a, wide, s); break;
+    case OP_JACOBI: launch_mode<OP_JACOBI>(m, depth, dtype, a, wide, s); break;
+    case OP_CHEB: launch_mode<OP_CHEB>(m, depth, dtype, a, wide, s); break;
+    case OP_DIAG: launch_mode<OP_DIAG>(m, depth, dtype, a, wide, s); break;
+  }
+}
+
+// Work lists of the march: per tet (those above the coarsest level first),
+// tiles (i0, j0) of 30 columns (sitems; 60 for the two-column-set kernel:
+// mitems) x 16 rows, each tile's planes 1 .. N-1-i0-j0 cut into segments of
+// kseg planes; longest segment first within a class (korder 1: by plane
+// window).  kseg is halved (down to 4) while a class would have fewer items
+// than two per resident block.
+static void march_items(const Mesh& m, Depth& D, int cols, std::vector<int4>& out, int& n_nc) {
   const int ns = (int)D.slot_tet.size();
-  D.h_pairs.clear();
-  for (int s = 0; s < ns; ++s) D.h_pairs.push_back(make_int2(s, -1));
   const long long target = (long long)(m.num_sms > 0 ? m.num_sms : 152) * 3 * 2;
   constexpr int kTileJ = kWarps * kRowsW;
   std::vector<int4> lists[2];
@@ -514,7 +595,7 @@ void build_march_items(const Mesh& m, Depth& D) {
       for (int s : slots) {
         const int N = D.h_tets[s].N;
         for (int j0 = 1; j0 <= N - 2; j0 += kTileJ)
-          for (int i0 = 1; i0 + j0 <= N - 2; i0 += kCols) c += (N - 1 - (i0 + j0) + ks - 1) / ks;
+          for (int i0 = 1; i0 + j0 <= N - 2; i0 += cols) c += (N - 1 - (i0 + j0) + ks - 1) / ks;
       }
       return c;
     };
@@ -524,7 +605,7 @@ void build_march_items(const Mesh& m, Depth& D) {
     for (int s : slots) {
       const int N = D.h_tets[s].N;
       for (int j0 = 1; j0 <= N - 2; j0 += kTileJ)
-        for (int i0 = 1; i0 + j0 <= N - 2; i0 += kCols) {
+        for (int i0 = 1; i0 + j0 <= N - 2; i0 += cols) {
           const int top = N - 1 - (i0 + j0);
           for (int k0 = 1; k0 <= top; k0 += ks) {
             const int k1 = std::min(top, k0 + ks - 1);
@@ -538,12 +619,19 @@ void build_march_items(const Mesh& m, Depth& D) {
     std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
     for (auto& e : its) lists[cls].push_back(e.second);
   }
-  D.h_sitems = lists[0];
-  D.n_sitems_nc = (int)lists[0].size();
-  D.h_sitems.insert(D.h_sitems.end(), lists[1].begin(), lists[1].end());
+  out = lists[0];
+  n_nc = (int)lists[0].size();
+  out.insert(out.end(), lists[1].begin(), lists[1].end());
+}
+
+void build_march_items(const Mesh& m, Depth& D) {
+  const int ns = (int)D.slot_tet.size();
+  D.h_pairs.clear();
+  for (int s = 0; s < ns; ++s) D.h_pairs.push_back(make_int2(s, -1));
+  march_items(m, D, kCols, D.h_sitems, D.n_sitems_nc);
   D.n_sitems = (int)D.h_sitems.size();
-  D.h_mitems.clear();
-  D.n_mitems = D.n_mitems_nc = 0;
+  march_items(m, D, kCols + kSet, D.h_mitems, D.n_mitems_nc);
+  D.n_mitems = (int)D.h_mitems.size();
 }
 
 }  // namespace hhg

@@ -86,9 +86,12 @@ void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_kor
     for (int w = 0; w < warm; ++w) apply_scaled(m, 0, dtype, u, y, s);
     // two passes over the candidates (volume kernel x segmentation x order),
     // each candidate's better pass counts
-    double cand_ms[2][2][3];
+    // volume kernels: tile march, column march, and for FP32 the column
+    // march with two column sets per lane
+    const int n_vk = elem_size(dtype) == 8 ? 2 : 3;
+    double cand_ms[3][2][3];
     for (int pass = 0; pass < 2; ++pass)
-      for (int vk = 0; vk < 2; ++vk)
+      for (int vk = 0; vk < n_vk; ++vk)
         for (int oi = 0; oi < 2; ++oi)
           for (int ki = 0; ki < 3; ++ki) {
             m.vkernel = vk;
@@ -97,7 +100,7 @@ void autotune(Mesh& m, int dtype, const char* cache, int* out_kseg, int* out_kor
             const double med = timed_median(5);
             cand_ms[vk][oi][ki] = pass == 0 ? med : std::min(cand_ms[vk][oi][ki], med);
           }
-    for (int vk = 0; vk < 2; ++vk)
+    for (int vk = 0; vk < n_vk; ++vk)
       for (int oi = 0; oi < 2; ++oi)
         for (int ki = 0; ki < 3; ++ki)
           if (best_ms < 0 || cand_ms[vk][oi][ki] < best_ms) {

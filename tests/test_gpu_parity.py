@@ -362,10 +362,17 @@ def test_autotune_keeps_results_identical(H, tmp_path):
     r1 = H.hhg_autotune(c.m.h, 1, cache)
     assert r1["kseg"] in (16, 32, 64) and r1["korder"] in (0, 1) and r1["best_ms"] > 0
     r2 = H.hhg_autotune(c.m.h, 1, cache)  # cache hit
-    assert (r2["kseg"], r2["korder"]) == (r1["kseg"], r1["korder"])
+    assert (r2["kseg"], r2["korder"], r2["vkernel"]) == (r1["kseg"], r1["korder"], r1["vkernel"])
     y1 = torch.empty_like(ud)
     H.hhg_apply_scaled(c.m.h, 0, ud, y1, 1)
-    # the work split changes, the per-node arithmetic does not
+    # the column marches (one or two column sets per lane) round every node
+    # alike whatever the work split; the tile march sums in another order
+    if r1["vkernel"] in (1, 2):
+        assert torch.equal(y0, y1)
+    else:
+        assert _rel(y1.double().cpu().numpy(), y0.double().cpu().numpy()) <= 1e-6
+    H.hhg_set_option(c.m.h, "vkernel", 1)
+    H.hhg_apply_scaled(c.m.h, 0, ud, y1, 1)
     assert torch.equal(y0, y1)
 
 
@@ -575,3 +582,83 @@ def test_zero_sweeps_and_single_depth_mesh(H):
     x = np.linalg.solve(A.toarray(), f[c2.lm.unknowns])
     assert _rel(c2.back(u)[c2.lm.unknowns], x) <= 1e-10 and st["iterations"] <= 2
     c2.m.close()
+
+
+# The three volume kernels of the scaled operator: the tile march (vkernel
+# 0), the column march (1) and the column march with two column sets per
+# lane in packed FP32x2 arithmetic (2; FP64 runs as 1).  Meshes with several
+# 30- and 60-column tiles per tet and ragged last tiles.
+VK_MESHES = {"kuhn_cube_l6": (I.kuhn_cube, 6, 2, I.k_cube), "cube24_l5": (I.cube24, 5, 2, I.k_large)}
+
+
+@pytest.fixture(scope="module", params=list(VK_MESHES))
+def vk_case(request, H):
+    mesh, level, coarsest, kf = VK_MESHES[request.param]
+    V, T = mesh()
+    c = Case(H, V, T, level, coarsest, kf)
+    c.f_or = np.where(c.dir, 0.0, np.sin(7 * c.lm.coords[:, 0]) + c.lm.coords[:, 2])
+    return c
+
+
+@pytest.mark.parametrize("vkernel", [0, 1, 2])
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_volume_kernels_apply_residual_jacobi(H, vk_case, vkernel, dtype):
+    c = vk_case
+    H.hhg_set_option(c.m.h, "vkernel", vkernel)
+    try:
+        tol = 1e-12 if dtype == H.HHG_F64 else 1e-6
+        rnd = (lambda x: x) if dtype == H.HHG_F64 else _f32
+        u, f = rnd(c.rand_or), rnd(c.f_or)
+        kp = c.kprec(dtype)
+        ud, fd = c.dev(u, dtype), c.dev(f, dtype)
+        y = torch.empty_like(ud)
+        H.hhg_apply_scaled(c.m.h, 0, ud, y, dtype)
+        Au = c.lm.apply(u, kp, "scaled")
+        assert _rel(c.back(y), Au) <= tol, _rel(c.back(y), Au)
+        H.hhg_residual(c.m.h, 0, fd, ud, y, dtype)
+        want = np.where(c.dir, 0.0, f - Au)
+        assert _rel(c.back(y), want) <= tol, _rel(c.back(y), want)
+        # one damped Jacobi sweep: u + omega (f - A u) / diag(A)
+        Dg = np.ones(c.lm.n)
+        Dg[c.lm.unknowns] = c.lm.system(kp, "scaled").diagonal()
+        H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_JACOBI, 1, 0.6, fd, ud, dtype)
+        want = np.where(c.dir, 0.0, u + 0.6 * (f - Au) / Dg)
+        assert _rel(c.back(ud), want) <= (1e-12 if dtype == H.HHG_F64 else 1e-5)
+    finally:
+        H.hhg_set_option(c.m.h, "vkernel", 1)
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_two_column_sets_chebyshev_sweeps_match_the_column_march(H, vk_case, dtype):
+    """Three Chebyshev sweeps (the smoother's recurrence carries d between
+    sweeps) with vkernel 2 against vkernel 1 (itself checked against the
+    oracle through the V-cycle tests)."""
+    c = vk_case
+    f = c.dev(_f32(c.f_or), dtype)
+    outs = []
+    for vk in (1, 2):
+        H.hhg_set_option(c.m.h, "vkernel", vk)
+        ud = c.dev(_f32(c.rand_or), dtype)
+        H.hhg_smooth(c.m.h, 0, H.HHG_SMOOTH_CHEBYSHEV, 3, 0.6, f, ud, dtype)
+        outs.append(c.back(ud))
+    H.hhg_set_option(c.m.h, "vkernel", 1)
+    assert _rel(outs[1], outs[0]) <= 1e-5, _rel(outs[1], outs[0])
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_one_and_two_column_sets_round_alike(H, vk_case, dtype):
+    """The packed FP32x2 march rounds each component as the scalar march
+    does (same operations in the same order, no contraction): apply and
+    residual bitwise equal."""
+    c = vk_case
+    ud, fd = c.dev(_f32(c.rand_or), dtype), c.dev(_f32(c.f_or), dtype)
+    outs = []
+    for vk in (1, 2):
+        H.hhg_set_option(c.m.h, "vkernel", vk)
+        y, r = torch.empty_like(ud), torch.empty_like(ud)
+        H.hhg_apply_scaled(c.m.h, 0, ud, y, dtype)
+        H.hhg_residual(c.m.h, 0, fd, ud, r, dtype)
+        outs.append((y, r))
+    H.hhg_set_option(c.m.h, "vkernel", 1)
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
