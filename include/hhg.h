@@ -363,8 +363,8 @@ int hhg_solve(hhg_mesh mesh, const hhg_solve_params* p, const double* f_dev, dou
  * "korder" (0: longest item first, 1: items ordered by plane window) -- both
  * rebuild the work lists and synchronise the device --, "vkernel" (1: the
  * column-march volume kernel, 2: the same with two column sets per lane in
- * packed FP32x2 arithmetic for the FP32 dtypes, FP64 running as 1; 0: the
- * tile-march one), "cheb_degree",
+ * packed FP32x2 arithmetic for the FP32 apply, the other modes and FP64
+ * running as 1; 0: the tile-march one), "cheb_degree",
  * "cheb_lo", "cheb_hi" (Chebyshev interval as fractions of lambda_max) and
  * "power_its" (lambda_max estimate).  Unknown keys or out-of-range values:
  * HHG_ERR_ARG. */

@@ -193,8 +193,16 @@ struct Lanes<float, 2> {
   }
 };
 
+// resident blocks per SM the registers are budgeted for (every variant
+// without spills): more warps hide the latency of the dependent flux chains
+constexpr int march_min_blocks(size_t es, int mode, int p) {
+  return es == 8 ? 2
+         : p == 2 ? (mode == OP_JACOBI || mode == OP_CHEB || mode == OP_RESID ? 3 : 4)
+                  : (mode == OP_JACOBI || mode == OP_CHEB ? 3 : 4);
+}
+
 template <class T, class KT, int MODE, int P>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 || MODE == OP_JACOBI || MODE == OP_CHEB || P == 2 ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, march_min_blocks(sizeof(T), MODE, P))
     march_kernel(DepthDev D, const T* __restrict__ sten, MarchPtrs p, int n_items) {
   using G = Geo<T, KT, MODE, P>;
   using L = Lanes<T, P>;
@@ -563,9 +571,11 @@ void init_march_configs(int dtype) {
   }
 }
 
-// vkernel 2: FP32 runs the march with two column sets per lane (FP64 keeps one)
+// vkernel 2: the FP32 apply (and diagonal) run the march with two column
+// sets per lane; the modes that also stream f (residual, Jacobi, Chebyshev)
+// keep one, which measures faster for them; FP64 keeps one
 void launch_march(const Mesh& m, int depth, int dtype, OpMode mode, const OpArgs& a, cudaStream_t s) {
-  const bool wide = m.vkernel == 2;
+  const bool wide = m.vkernel == 2 && (mode == OP_APPLY || mode == OP_DIAG);
   switch (mode) {
     case OP_APPLY: launch_mode<OP_APPLY>(m, depth, dtype, a, wide, s); break;
     case OP_RESID: launch_mode<OP_RESID>(m, depth, dtype, a, wide, s); break;
