@@ -67,10 +67,14 @@ CPU_SOLVE_LEVEL = 5  # its GMG-CG sample (125,055 unknowns)
 # kernel by kernel: the volume kernel by stored nodes, the interface kernel by
 # interface copies), one kernel per ncu call (profiles/apply_bf16k_cube24_l8_traffic.md).
 NCU_TRAFFIC = {
-    "bf16k_cube24": {"sha": "edf6519a5d4ab118", "volume_bytes_per_node": (605144064 + 275206144) / 68693016,
-                     "interface_bytes_per_copy": (307726848 + 41057024) / (24 * (257 * 258 * 259 // 6 - 255 * 254 * 253 // 6)),
-                     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 24-tet cube level 8, march_kernel and "
-                               "boundary_only_kernel captured separately, scaled to this workload per kernel unit"},
+    # the column march with two column sets per lane (vkernel 2), the kernel
+    # the autotuner picks for this workload
+    "bf16k_cube24": {"sha": "047c2eeababe5719", "vkernel": 2,
+                     "volume_bytes_per_node": (556425472 + 262863616) / 68693016,
+                     "interface_bytes_per_copy": (307681024 + 41054208) / (24 * (257 * 258 * 259 // 6 - 255 * 254 * 253 // 6)),
+                     "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, 24-tet cube level 8, "
+                               "march_kernel<float,bf16,APPLY,2> and boundary_only_kernel captured in separate ncu runs, "
+                               "scaled to this workload per kernel unit"},
 }
 
 
@@ -98,9 +102,12 @@ def interface_copies(T, level):
     return len(T) * ((N + 1) * (N + 2) * (N + 3) // 6 - (N - 1) * (N - 2) * (N - 3) // 6)
 
 
-def _traffic(dtype_name, n_stored, n_copies):
+def _traffic(dtype_name, n_stored, n_copies, vkernel=None):
+    """DRAM bytes of one apply from the recorded per-unit counters, or None
+    when the kernels changed since (source hash) or another volume kernel
+    runs."""
     rec = NCU_TRAFFIC.get(dtype_name)
-    if not rec or rec["sha"] != _kernel_sha():
+    if not rec or rec["sha"] != _kernel_sha() or (vkernel is not None and vkernel != rec.get("vkernel", vkernel)):
         return None, None
     return rec["volume_bytes_per_node"] * n_stored + rec["interface_bytes_per_copy"] * n_copies, rec["source"]
 
@@ -521,6 +528,46 @@ def batch_bench(H, I, torch, flush):
 TENSOR_LEVELS = (3, 4, 5, 6, 7)  # the paper's L = 1 .. 5 on the 12-tet cube
 
 
+def tensor_apply_timed(H, m, n, level, torch, flush, reps=10):
+    """FP32 tensor apply (the mesh's tensor coefficient set) against its HBM
+    roofline: algorithmic bytes u, the six k_m and y (32 B per node); the
+    kernel streams the seven edge weights instead of the six k_m (36 B per
+    node), so the fraction is a lower bound of the kernel's own."""
+    x = torch.rand(n, device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
+    ts = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    peaks, src = _peaks()
+    ach = 32 * n / (ms * 1e-3) / 1e9
+    return {"level": level, "stored_nodes": n, "ms": ms,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_node": 32,
+                         "kernel_bytes_per_node": 36, "peak_source": f"{src} hbm_gbs (burst)"}}
+
+
+def tensor_apply_only(H, I, torch, flush, level=TENSOR_LEVELS[-1]):
+    """Only the FP32 tensor apply of the tensor table's finest level (the
+    12-tet cube, the paper's K): the case its kernels are profiled on."""
+    V, T = I.cube12()
+    m = H.Mesh(V, T, level, 1)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_tensor_coefficient(m.h, torch.tensor(np.ascontiguousarray(I.K_tensor(xyz).T), device="cuda"))
+    out = tensor_apply_timed(H, m, n, level, torch, flush)
+    m.close()
+    return out
+
+
 def tensor_table(H, I, torch, flush, levels=TENSOR_LEVELS):
     """Shape of the paper's tensor test (Sec. 7.3, Tab. "divK4"): the 12-tet
     cube, its permeability tensor K, multigrid V(3,3) (FP64) until the
@@ -554,26 +601,7 @@ def tensor_table(H, I, torch, flush, levels=TENSOR_LEVELS):
                      "cycles": st["iterations"], "tts_ms": st["time_ms"]})
         prev = err
         if level == levels[-1]:
-            x = torch.rand(n, device="cuda", dtype=torch.float32)
-            y = torch.empty_like(x)
-            for _ in range(3):
-                H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
-            ts = []
-            for i in range(10):
-                flush.fill_(float(i))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                H.hhg_apply_tensor(m.h, 0, x, y, H.HHG_F32)
-                b.record()
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b))
-            ms = float(np.mean(ts))
-            peaks, src = _peaks()
-            ach = 32 * n / (ms * 1e-3) / 1e9
-            apply = {"level": level, "stored_nodes": n, "ms": ms,
-                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                  "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_node": 32,
-                                  "kernel_bytes_per_node": 36}}
+            apply = tensor_apply_timed(H, m, n, level, torch, flush)
         m.close()
     return {"workload": "unit cube, 12 macro-tets, K = the paper's tensor (Sec. 7.3), u* = sin(pi x) sin(pi y) "
                         "sin(pi z); V(3,3) (damped Jacobi) to a 1e-9 residual reduction, FP64",
@@ -856,6 +884,10 @@ def main():
     ap.add_argument("--no-table", action="store_true", help="skip the multigrid tables (scalar and tensor)")
     ap.add_argument("--only-learned", action="store_true",
                     help="run only the learned-smoother section (C4) and print its JSON")
+    ap.add_argument("--only-tensor", action="store_true",
+                    help="run only the FP32 tensor apply of the tensor table's finest level and print its JSON")
+    ap.add_argument("--vkernel", type=int, choices=[0, 1, 2], default=None,
+                    help="fix the volume kernel of the scaled apply instead of autotuning it (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -877,6 +909,11 @@ def main():
         if rank == 0:
             print(json.dumps({"learned": out}))
         return
+    if args.only_tensor:
+        out = tensor_apply_only(H, I, torch, flush)
+        if rank == 0:
+            print(json.dumps({"tensor_apply_fp32": out}))
+        return
 
     t_setup = time.perf_counter()
     m, T, n, k, u = c5_setup(H, I, torch, args.level)
@@ -884,7 +921,10 @@ def main():
     setup_s = time.perf_counter() - t_setup
     y = torch.empty_like(u)
     DT = H.HHG_F32_KBF16
-    tune = None if args.no_tune else H.hhg_autotune(m.h, DT)
+    fixed = args.no_tune or args.vkernel is not None
+    if args.vkernel is not None:
+        H.hhg_set_option(m.h, "vkernel", args.vkernel)
+    tune = None if fixed else H.hhg_autotune(m.h, DT)
     for _ in range(max(3, args.warmup)):
         H.hhg_apply_scaled(m.h, 0, u, y, DT, stream)
     torch.cuda.synchronize()
@@ -911,14 +951,14 @@ def main():
     peaks, src = _peaks()
     algo_bytes = 10 * unknowns  # read u (FP32), k (BF16); write y (FP32): every unknown once
     achieved = algo_bytes / (ms * 1e-3) / 1e9
-    traffic, tsrc = _traffic("bf16k_cube24", n, interface_copies(T, args.level))
+    traffic, tsrc = _traffic("bf16k_cube24", n, interface_copies(T, args.level), int(H.hhg_get_option(m.h, "vkernel")))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
             "peak_source": f"{src} hbm_gbs (burst)",
-            "kernel": "volume kernel chosen by the autotuner (march_kernel<float,__nv_bfloat16,APPLY>, the column "
-                      "march, or scaled_op_kernel, the tile march) + boundary_only_kernel (interface rows, concurrent on "
-                      "a forked stream); achieved = algorithmic bytes / CUDA-event time of the pair on the caller's "
-                      "stream",
+            "kernel": "volume kernel chosen by the autotuner (march_kernel<float,__nv_bfloat16,APPLY,P>, the column "
+                      "march with P = 1 or 2 column sets per lane, or scaled_op_kernel, the tile march) + "
+                      "boundary_only_kernel (interface rows, on a forked stream); achieved = algorithmic bytes / "
+                      "CUDA-event time of the pair on the caller's stream",
             "algorithmic_bytes_per_launch": algo_bytes, "algorithmic_bytes_per_unknown": 10,
             "stored_node_bytes_fraction": 10 * n / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
 
@@ -937,7 +977,7 @@ def main():
 
     # the other operators on the same workload: FP32 k, the nodal-integration
     # apply (the paper's cost comparison), FP64 against the FP64-ALU peak
-    tune32 = None if args.no_tune else H.hhg_autotune(m.h, H.HHG_F32)
+    tune32 = None if fixed else H.hhg_autotune(m.h, H.HHG_F32)
     f32_ms = events_ms(torch, stream, flush, lambda: H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32, stream), 10)
     if tune is not None:
         H.hhg_set_option(m.h, "vkernel", tune["vkernel"])
