@@ -21,7 +21,8 @@ the shift of the discrete solution when k is rounded to bfloat16, end-to-end
 applies from pinned host buffers next to the measured pinned-copy bandwidth,
 and the FP64 / FP32 multiply-add peaks that bound the ALU-limited kernels.
 Extra keys: the 6-tet cube at level 8 (FP32 k), the multigrid tables, the
-48 random tetrahedra and the learned smoother.  cpu_baseline: the FP64
+48 random tetrahedra (independent, levels 5..8), 48 tetrahedra sharing
+faces (one level) and the learned smoother.  cpu_baseline: the FP64
 oracle on every host core (one process per core) on a smaller level of the
 same workload.
 
@@ -525,6 +526,54 @@ def batch_bench(H, I, torch, flush):
     return out
 
 
+CONFORMING_LEVEL = 7
+
+
+def conforming_batch_bench(H, I, torch, flush, level=CONFORMING_LEVEL):
+    """48 tetrahedra that share faces (the unit cube as 2 x 2 x 2 half cubes
+    of 6 Kuhn tetrahedra each, inner vertices moved at random), all at one
+    level, k = 1 + 0.9 tanh(Fourier field): the batched apply of all 48 tets
+    with the interface rows of their 72 shared faces, and the mixed-precision
+    GMG-CG solve."""
+    V, T = I.cube48()
+    m = H.Mesh(V, T, level, 2)
+    off, lev, n = m.layout(0)
+    xyz = m.coords(0)
+    H.hhg_set_coefficient(m.h, torch.tensor(I.k_batched(1)(xyz), device="cuda"))
+    tune = H.hhg_autotune(m.h, H.HHG_F32)
+    u = torch.rand(n, device="cuda", dtype=torch.float32)
+    mask = torch.empty_like(u)
+    H.hhg_residual(m.h, 0, torch.ones_like(u), torch.zeros_like(u), mask, H.HHG_F32)
+    u *= mask
+    y = torch.empty_like(u)
+    for _ in range(3):
+        H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32)
+    ts = []
+    for i in range(20):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.hhg_apply_scaled(m.h, 0, u, y, H.HHG_F32)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    unknowns = unknowns_of(T, level)
+    peaks, src = _peaks()
+    f = torch.tensor(np.sin(3 * xyz[:, 0]) * np.cos(2 * xyz[:, 1]) + xyz[:, 2], device="cuda") * mask.double()
+    out = {"workload": f"48 tetrahedra sharing faces (2 x 2 x 2 half cubes x 6 Kuhn tets, inner vertices jittered, "
+                       f"seed 3), level {level}, k = 1 + 0.9 tanh(Fourier field)",
+           "level": level, "stored_nodes": n, "unknowns": unknowns,
+           "interface_copies": interface_copies(T, level), "autotune": tune,
+           "apply_ms": ms, "apply_gdofs": unknowns / (ms * 1e-3) / 1e9,
+           "apply_hbm_frac": 12 * unknowns / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    sol, _, _ = solve_runs(H, torch, m, n, f, (("solve_mixed", H.HHG_SOLVE_MIXED, H.HHG_SMOOTH_JACOBI),
+                                                ("solve_fp64", H.HHG_SOLVE_FP64, H.HHG_SMOOTH_JACOBI)))
+    out.update(sol)
+    m.close()
+    return out
+
+
 TENSOR_LEVELS = (3, 4, 5, 6, 7)  # the paper's L = 1 .. 5 on the 12-tet cube
 
 
@@ -605,7 +654,8 @@ def tensor_table(H, I, torch, flush, levels=TENSOR_LEVELS):
         m.close()
     return {"workload": "unit cube, 12 macro-tets, K = the paper's tensor (Sec. 7.3), u* = sin(pi x) sin(pi y) "
                         "sin(pi z); V(3,3) (damped Jacobi) to a 1e-9 residual reduction, FP64",
-            "rows": rows, "apply_fp32": apply}
+            "rows": rows, "apply_fp32": apply,
+            "apply_fp32_next_level": tensor_apply_only(H, I, torch, flush, levels[-1] + 1)}
 
 
 
@@ -1060,6 +1110,7 @@ def main():
         m2.close()
         if not args.no_solve:
             out["batch"] = batch_bench(H, I, torch, flush)
+            out["batch_conforming"] = conforming_batch_bench(H, I, torch, flush)
         if not args.no_learned:
             out["learned"] = learned_bench(H, I, torch, stream, flush)
 

@@ -59,6 +59,39 @@ def kuhn_cube():
     return V, np.array(T, dtype=np.int32)
 
 
+def cube48(seed=3, jitter=0.08):
+    """Unit cube as a conforming mesh of 48 tetrahedra with shared faces: the
+    2 x 2 x 2 grid of half cubes, each split into the 6 Kuhn tetrahedra of
+    kuhn_cube (the same path orientation everywhere, so neighbouring half
+    cubes meet face to face), then the grid's vertices moved at random
+    (seeded): the centre in all three directions, face centres within their
+    face, edge midpoints along their edge, by up to `jitter` (the half-cube
+    edge is 0.5); the corners and the cube's boundary stay.  A batched mesh
+    whose tetrahedra share faces, edges and vertices."""
+    rng = np.random.default_rng(seed)
+    grid = list(itertools.product(range(3), repeat=3))  # index = 9x+3y+z
+    V = np.array(grid, dtype=np.float64) * 0.5
+    for n, g in enumerate(grid):
+        for a in range(3):
+            if g[a] == 1:  # interior coordinate of this vertex's face / edge / the centre
+                V[n, a] += rng.uniform(-jitter, jitter)
+
+    def vid(p):
+        return 9 * p[0] + 3 * p[1] + p[2]
+
+    T = []
+    for base in itertools.product(range(2), repeat=3):
+        for perm in itertools.permutations(range(3)):
+            p = list(base)
+            path = [vid(p)]
+            for a in perm:
+                p = list(p)
+                p[a] += 1
+                path.append(vid(p))
+            T.append(path)
+    return V, np.array(T, dtype=np.int32)
+
+
 def cube12():
     """Unit cube: body centre + 2 triangles per face, coned to the centre (12 tets)."""
     corners = np.array(list(itertools.product([0, 1], repeat=3)), dtype=np.float64)

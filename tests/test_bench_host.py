@@ -23,7 +23,7 @@ def test_unknown_count_matches_the_oracle_meshes():
     from paper_1709_06793_gb300 import inputs as I
     _, T = I.kuhn_cube()
     assert bench.unknowns_of(T, 8) == 255 ** 3
-    for mesh, levels in ((I.cube24, (1, 2, 3, 4)), (I.cube12, (1, 2, 3)), (I.unit_tet, (2, 3))):
+    for mesh, levels in ((I.cube24, (1, 2, 3, 4)), (I.cube12, (1, 2, 3)), (I.cube48, (1, 2, 3)), (I.unit_tet, (2, 3))):
         V, T = mesh()
         for level in levels:
             lm = O.LevelMesh(O.MacroMesh(V, T), level)

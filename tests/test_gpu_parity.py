@@ -89,6 +89,7 @@ MESHES = {
     "kuhn_cube_l4": (I.kuhn_cube, 4, 2, I.k_cube),
     "cube24_l3": (I.cube24, 3, 1, I.k_large),
     "cube12_l3": (I.cube12, 3, 1, I.k_cube),
+    "cube48_l3": (I.cube48, 3, 1, I.k_batched(1)),  # 48 tets sharing faces (a batch with interfaces)
 }
 
 
@@ -588,7 +589,8 @@ def test_zero_sweeps_and_single_depth_mesh(H):
 # 0), the column march (1) and the column march with two column sets per
 # lane in packed FP32x2 arithmetic (2; FP64 runs as 1).  Meshes with several
 # 30- and 60-column tiles per tet and ragged last tiles.
-VK_MESHES = {"kuhn_cube_l6": (I.kuhn_cube, 6, 2, I.k_cube), "cube24_l5": (I.cube24, 5, 2, I.k_large)}
+VK_MESHES = {"kuhn_cube_l6": (I.kuhn_cube, 6, 2, I.k_cube), "cube24_l5": (I.cube24, 5, 2, I.k_large),
+             "cube48_l5": (I.cube48, 5, 2, I.k_batched(1))}
 
 
 @pytest.fixture(scope="module", params=list(VK_MESHES))

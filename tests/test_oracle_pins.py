@@ -7,6 +7,7 @@ that a dropped term, a wrong sign, index or vertex order fails one of them.
 import itertools
 import math
 import os
+from collections import Counter
 
 import numpy as np
 import pytest
@@ -371,3 +372,18 @@ def test_manufactured_rhs_is_minus_div_k_grad_u():
         e[a] = h
         div += (flux(x + e)[:, a] - flux(x - e)[:, a]) / (2 * h)
     assert np.allclose(I.f_cube_sine(x), -div, rtol=1e-6, atol=1e-6)
+
+
+def test_cube48_is_a_conforming_partition_of_the_unit_cube():
+    """The 48-tetrahedron mesh: volumes sum to 1, every tet is non-degenerate,
+    inner faces are shared by exactly two tets and the 48 boundary faces lie
+    on the cube's faces (so the domain is the unit cube)."""
+    V, T = I.cube48()
+    vol = [abs(np.linalg.det(np.stack([V[t[1]] - V[t[0]], V[t[2]] - V[t[0]], V[t[3]] - V[t[0]]]))) / 6 for t in T]
+    assert abs(sum(vol) - 1.0) < 1e-12 and min(vol) > 0.01
+    faces = Counter(tuple(sorted(f)) for t in T for f in itertools.combinations(t, 3))
+    assert sorted(Counter(faces.values()).items()) == [(1, 48), (2, 72)]
+    for f, c in faces.items():
+        if c == 1:
+            P = V[list(f)]
+            assert any(np.all(np.abs(P[:, a] - P[0, a]) < 1e-15) and P[0, a] in (0.0, 1.0) for a in range(3))
