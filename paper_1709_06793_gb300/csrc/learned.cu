@@ -170,13 +170,17 @@ __global__ void __launch_bounds__(kThreads, 2)
 //            the packed (a0, a1) pair at point p + tau, W1 lives in registers;
 //   layer 2  P[p][tau] = sum_c h[p][c] W2[tau][c]: the FP32 accumulators of
 //            layer 1 (after ReLU, rounded to BF16) are exactly the A fragment
-//            of this product; 27 taps padded to 32 columns;
-//   output   ch(x) = sum_tau P[x + tau][tau], gathered from shared memory.
+//            of this product; 27 taps padded to 32 columns; P is kept in
+//            shared memory as BF16 (54 KB instead of 109 KB), so that two
+//            blocks of 8 warps share an SM and one block's contractions
+//            overlap the other's gathers and input loads;
+//   output   ch(x) = sum_tau P[x + tau][tau], gathered from shared memory
+//            (FP32 sums, three partial sums over the tap planes).
 constexpr int kHP = kBH * kBH * kBH;          // 1000 hidden points
 constexpr int kMT = (kHP + 15) / 16;          // 63 row tiles
 constexpr int kPS = kTaps;                    // P row stride (odd: conflict-free gather)
-constexpr int kTcThreads = 512;
-constexpr size_t kTcSmem = (size_t)kBF * kBF * kBF * 4 + (size_t)kMT * 16 * kPS * 4;
+constexpr int kTcThreads = 256;
+constexpr size_t kTcSmem = (size_t)kBF * kBF * kBF * 4 + (size_t)kMT * 16 * kPS * 2;
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -193,13 +197,13 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
 }
 
 template <int OUT>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     conv_fwd_tc_kernel(DepthDev D, const int4* __restrict__ tiles, int n_tiles, const __nv_bfloat16* __restrict__ w,
                        const float* __restrict__ r, const float2* __restrict__ feat, const float* src, float* dst,
                        float* __restrict__ craw) {
   extern __shared__ __align__(16) unsigned char smb[];
   unsigned* X2 = reinterpret_cast<unsigned*>(smb);
-  float* P = reinterpret_cast<float*>(smb + kBF * kBF * kBF * 4);
+  __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(smb + kBF * kBF * kBF * 4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   auto wv = [&](int q) { return __bfloat162float(w[q]); };
@@ -303,12 +307,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int tau = 8 * nt + 2 * t;
         const int r0 = (16 * mt + g) * kPS, r1 = (16 * mt + g + 8) * kPS;
         if (tau < kTaps) {
-          P[r0 + tau] = pp[0];
-          P[r1 + tau] = pp[2];
+          P[r0 + tau] = __float2bfloat16(pp[0]);
+          P[r1 + tau] = __float2bfloat16(pp[2]);
         }
         if (tau + 1 < kTaps) {
-          P[r0 + tau + 1] = pp[1];
-          P[r1 + tau + 1] = pp[3];
+          P[r0 + tau + 1] = __float2bfloat16(pp[1]);
+          P[r1 + tau + 1] = __float2bfloat16(pp[3]);
         }
       }
     }
@@ -318,9 +322,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int i = i0 + oi, j = j0 + oj, k = k0 + ok;
       if (!in_set(N, i, j, k)) continue;
       const int hb = (oi + 1) + kBH * (oj + 1) + kBH * kBH * (ok + 1);
-      float acc = 0.f;
+      float a3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int tau = 0; tau < kTaps; ++tau) acc += P[(hb + tap_off(tau, kBH)) * kPS + tau];
+      for (int tau = 0; tau < kTaps; ++tau) a3[tau / 9] += __bfloat162float(P[(hb + tap_off(tau, kBH)) * kPS + tau]);
+      const float acc = a3[0] + a3[1] + a3[2];
       const long long idx = td.base + node_offset(N, i, j, k);
       if (OUT == 0) {
         dst[idx] = acc;
@@ -702,7 +707,7 @@ void launch_fwd(Mesh& m, Learned& L, int d, const float* r, const float* src, fl
   const int g = std::min(nt, L.nblk);
   const DepthDev& DD = m.depth[d].dev;
   if (L.bf16 && (OUT == 1 ? L.tc : L.tc_all))
-    conv_fwd_tc_kernel<OUT><<<std::min(nt, std::max(m.num_sms, 1)), kTcThreads, kTcSmem, s>>>(DD, X.tiles, nt, L.w16, r,
+    conv_fwd_tc_kernel<OUT><<<std::min(nt, 2 * std::max(m.num_sms, 1)), kTcThreads, kTcSmem, s>>>(DD, X.tiles, nt, L.w16, r,
                                                                                               X.feat, src, dst, craw);
   else if (L.bf16)
     conv_fwd_kernel<__nv_bfloat16, OUT><<<g, kThreads, kFwdSmem, s>>>(DD, X.tiles, nt, L.w16, r, X.feat, src, dst, craw);

@@ -141,10 +141,11 @@ def test_loss_and_gradient_match_oracle(H, bf16, d):
 
 @pytest.mark.parametrize("d", [0, 1])
 def test_tensor_core_forward_matches_oracle(H, d):
-    """BF16 forward on the tensor cores (mma.sync, BF16 inputs and hidden
-    activations, FP32 accumulation).  Rounding the two input channels and the
-    16 hidden channels to BF16 (2^-9 relative each) before FP32 sums of 54 and
-    432 products bounds the error by a few 2^-9 of the largest value: 1e-2."""
+    """BF16 forward on the tensor cores (mma.sync, BF16 inputs, hidden
+    activations and per-tap partial products, FP32 accumulation).  Rounding
+    the two input channels, the 16 hidden channels and the 27 per-tap
+    partials to BF16 (2^-9 relative each) before FP32 sums of 54, 16 and 27
+    terms bounds the error by a few 2^-9 of the largest value: 1e-2."""
     c = Case(H)
     rng = np.random.default_rng(80 + d)
     w = rng.normal(0, 0.3, LO.N_W).astype(np.float32)
