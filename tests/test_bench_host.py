@@ -58,3 +58,17 @@ def test_interface_copies_count_the_stored_face_nodes():
     _, T = I.cube24()
     assert bench.interface_copies(T, 1) == 24 * 10
     assert bench.interface_copies(T, 2) == 24 * (35 - 1)
+
+
+def test_traffic_record_applies_only_to_its_kernel_and_sources(monkeypatch):
+    """The stored counters scale per kernel unit while the sources hash to
+    the recorded value and the recorded volume kernel runs; otherwise the
+    bench reports no traffic."""
+    rec = bench.NCU_TRAFFIC["bf16k_cube24"]
+    monkeypatch.setattr(bench, "_kernel_sha", lambda: rec["sha"])
+    t, src = bench._traffic("bf16k_cube24", 1000, 10, rec["vkernel"])
+    assert abs(t - (rec["volume_bytes_per_node"] * 1000 + rec["interface_bytes_per_copy"] * 10)) < 1e-6 and src
+    other = 1 if rec["vkernel"] != 1 else 2
+    assert bench._traffic("bf16k_cube24", 1000, 10, other) == (None, None)
+    monkeypatch.setattr(bench, "_kernel_sha", lambda: "0" * 16)
+    assert bench._traffic("bf16k_cube24", 1000, 10, rec["vkernel"]) == (None, None)
