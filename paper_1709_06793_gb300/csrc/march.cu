@@ -29,11 +29,12 @@
 // its plane's group (cp.async.wait_group + __syncthreads).  No spin loop
 // waits on memory.
 //
-// FP32 also runs with two column sets per lane (P = 2): lane L holds columns
-// i0-1+L and i0+29+L of a 60-column tile, and the flux and row arithmetic
-// of both columns is one packed FP32x2 instruction (add / mul / fma .f32x2),
-// which halves the issued arithmetic per node; copies, shared loads and
-// shuffles stay per column, the row addressing is shared by both.
+// The FP32 apply and diagonal also run with two column sets per lane (P =
+// 2): lane L holds columns i0-1+L and i0+29+L of a 60-column tile, and the
+// flux and row arithmetic of both columns is one packed FP32x2 instruction
+// (add / mul / fma .f32x2), which halves the issued arithmetic per node;
+// copies, shared loads and shuffles stay per column, the row addressing is
+// shared by both.
 #include <algorithm>
 
 #include "hhg_internal.h"
